@@ -1,0 +1,159 @@
+"""Pins of the oracle's solvers (no GPU): dense direct solves, the deflated
+residual's orthogonality, textbook CG equivalences and the dt trends of the
+paper's Tables 1-3 (on Q1, so as trends only)."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import fem, mg, solvers
+from paper_2606_13429_gb300 import inputs
+
+
+def _f(asm, seed=0):
+    return inputs.rhs(seed, asm.mesh.n_unknowns)
+
+
+@pytest.mark.parametrize("d,n", [(2, 2), (2, 3), (2, 4), (2, 6), (3, 2), (3, 4)])
+def test_dense_cg_dcg_agree(d, n):
+    """P6: dense Cholesky == CG == DCG(exact inner) == DCG(MG inner) to 1e-10."""
+    for dt in [1e-1, 1e-4]:
+        asm = fem.assemble(d, n, dt)
+        f = _f(asm)
+        x_ref = solvers.dense_solve(asm, f)
+        sc = np.linalg.norm(x_ref)
+        x_cg, st = solvers.plain_cg(asm.matrix(), f, tol=1e-13)
+        assert np.linalg.norm(x_cg - x_ref) <= 1e-10 * sc
+        for rule in ["exact", "fixed", "adaptive"]:
+            o = solvers.FDCGOptions(inner_rule=rule, c=0.01)
+            x, st = solvers.FDCG(asm, o).solve(f, tol=1e-13)
+            assert st.converged
+            assert np.linalg.norm(x - x_ref) <= 1e-10 * sc, (rule, dt)
+
+
+def test_deflated_residual_orthogonal_to_S():
+    """P7: V^T r_i = 0 for r_i in the range of (I - pi_A)^T (from Eq.
+    defl_sys); exact inner to rounding, MG inner to ~ inner tolerance."""
+    asm = fem.assemble(2, 16, 1e-4)
+    f = _f(asm)
+    for rule, bound in [("exact", 1e-11), ("fixed", 1e-6)]:
+        S = solvers.FDCG(asm, solvers.FDCGOptions(inner_rule=rule))
+        A, V = S.A, S.V
+        st = solvers.SolveStats()
+        # replay the first iterations, checking V^T r after each update
+        f_D = f - A @ S.pi(f, 1e-10, st)
+        r = f_D.copy()
+        d = r.copy()
+        assert np.linalg.norm(V.T @ r) <= bound * np.linalg.norm(r)
+        for _ in range(6):
+            q = S.M_D(d, 1e-10, st)
+            dq = d @ q
+            alpha = (d @ r) / dq
+            r = r - alpha * q
+            assert np.linalg.norm(V.T @ r) <= bound * np.linalg.norm(f), rule
+            d = r - ((r @ q) / dq) * d
+
+
+def test_fcg_inf_exact_equals_cg_iterates():
+    """P13: with exact inner solves the deflated operator is fixed and
+    symmetric, so FCG(inf), FCG(1) and classical CG produce the same iterates."""
+    asm = fem.assemble(2, 12, 1e-3)
+    f = _f(asm)
+    hist = {}
+    for rec in ["fr", "fcg1", "fcg_inf"]:
+        o = solvers.FDCGOptions(inner_rule="exact", recurrence=rec)
+        x, st = solvers.FDCG(asm, o).solve(f, tol=1e-10)
+        hist[rec] = (np.array(st.history[:12]), st.outer_its, x)
+    h0 = hist["fr"][0]
+    for rec in ["fcg1", "fcg_inf"]:
+        assert np.allclose(hist[rec][0], h0, rtol=1e-8)
+        assert abs(hist[rec][1] - hist["fr"][1]) <= 1
+        assert np.linalg.norm(hist[rec][2] - hist["fr"][2]) <= 1e-10 * np.linalg.norm(hist["fr"][2])
+
+
+def test_condition_number_trend():
+    """P10 (Table 1 trend): kappa(A) grows like 1/dt for dt << h^2 and like
+    dt/h^2 for dt >> h^2 (U-shape); kappa_eff of the deflated operator stays
+    bounded as dt -> 0."""
+    n = 8
+    kap, keff = {}, {}
+    for dt in [1e0, 1e-2, 1e-4, 1e-6, 1e-8]:
+        asm = fem.assemble(2, n, dt)
+        A = asm.matrix().toarray()
+        ev = np.linalg.eigvalsh(A)
+        kap[dt] = ev[-1] / ev[0]
+        V = fem.V_matrix(asm.mesh).toarray()
+        Z = V.T @ A @ V
+        PiA = V @ np.linalg.solve(Z, V.T @ A)
+        AD = A @ (np.eye(A.shape[0]) - PiA)
+        AD = 0.5 * (AD + AD.T)
+        evd = np.linalg.eigvalsh(AD)
+        nz = evd[evd > 1e-9 * evd[-1]]
+        keff[dt] = nz[-1] / nz[0]
+    # small dt: kappa ~ 1/dt (x100 per two decades)
+    assert 50 < kap[1e-8] / kap[1e-6] < 200 and 50 < kap[1e-6] / kap[1e-4] < 200
+    # large dt: kappa grows again with dt (div-free modes of K_div, A ~ M/dt)
+    assert kap[1e0] > 3 * kap[1e-2]
+    # minimum near dt ~ h^2 = 1/64
+    assert min(kap, key=kap.get) == 1e-2
+    # kappa_eff bounded as dt -> 0
+    assert keff[1e-8] < 1.5 * keff[1e-6] and keff[1e-8] < 1e-5 * kap[1e-8]
+
+
+def test_iteration_trends():
+    """P11 (Table 2 trend): for dt << h^2 plain-CG counts grow as dt shrinks,
+    deflated-CG counts do not; P12 (Tables 2-3): DCG with the MG inner at
+    c_F = 0.01 needs the same outer count as with an exact inner solve (+-2)."""
+    asm_cache = {}
+    cg_its, dcg_its = {}, {}
+    for dt in [1e-4, 1e-6, 1e-8]:
+        asm = fem.assemble(2, 32, dt)
+        asm_cache[dt] = asm
+        f = _f(asm)
+        _, st = solvers.plain_cg(asm.matrix(), f)
+        cg_its[dt] = st.outer_its
+        _, st_e = solvers.FDCG(asm, solvers.FDCGOptions(inner_rule="exact")).solve(f)
+        _, st_m = solvers.FDCG(asm, solvers.FDCGOptions(inner_rule="fixed", c=0.01)).solve(f)
+        dcg_its[dt] = st_e.outer_its
+        assert abs(st_m.outer_its - st_e.outer_its) <= 2, dt
+        assert st_m.true_relres <= 1e-8 and st_e.true_relres <= 1e-8
+    # h^2 ~ 1e-3 here: plain CG grows steadily below it, DCG stays flat
+    assert cg_its[1e-8] > cg_its[1e-6] > cg_its[1e-4]
+    assert cg_its[1e-8] > 5 * cg_its[1e-4]
+    assert dcg_its[1e-8] <= dcg_its[1e-6] + 2
+    assert dcg_its[1e-8] < cg_its[1e-8] / 10
+
+
+@pytest.mark.parametrize("rule", ["fixed", "adaptive"])
+def test_true_residual_and_restart(rule):
+    """P14: true relative residual <= tol; with a very loose inner tolerance
+    the restart on the residual equation still delivers it."""
+    asm = fem.assemble(2, 16, 1e-5)
+    f = _f(asm, seed=3)
+    x_ref = solvers.dense_solve(asm, f)
+    for c in [0.01, 1.0]:
+        o = solvers.FDCGOptions(inner_rule=rule, c=c, max_restarts=5)
+        x, st = solvers.FDCG(asm, o).solve(f, tol=1e-8)
+        assert st.converged and st.true_relres <= 1e-8, (c, st.true_relres)
+        A = asm.matrix()
+        assert np.linalg.norm(f - A @ x) <= 1e-8 * np.linalg.norm(f)
+        assert np.linalg.norm(x - x_ref) <= 1e-4 * np.linalg.norm(x_ref)
+
+
+def test_initial_guess_and_zero_rhs():
+    asm = fem.assemble(2, 8, 1e-3)
+    f = _f(asm)
+    S = solvers.FDCG(asm)
+    x, st = S.solve(f, tol=1e-10)
+    x2, st2 = S.solve(f, tol=1e-10, x0=x)
+    assert st2.outer_its <= 1
+    z, st3 = S.solve(np.zeros_like(f))
+    assert not z.any() and st3.converged and st3.outer_its == 0
+
+
+def test_max_it_cap_reports_not_converged():
+    asm = fem.assemble(2, 16, 1e-2)
+    f = _f(asm)
+    x, st = solvers.FDCG(asm).solve(f, tol=1e-12, max_it=3)
+    assert st.outer_its == 3 and not st.converged
+    x, st = solvers.plain_cg(asm.matrix(), f, tol=1e-12, max_it=3)
+    assert st.outer_its == 3 and not st.converged
