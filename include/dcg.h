@@ -1,0 +1,204 @@
+/*
+ * dcg.h -- C ABI of the GB300 deflated-CG library (libdcg.so).
+ *
+ * The library solves the symmetric positive definite system
+ *
+ *     A x = f,   A = (1/dt) M_dev + K_div,
+ *
+ * that one implicit-Euler step of the pseudo-stress Stokes problem produces
+ * (Section 2.3, Eq. weak_IE; Section 3, Eq. pb_study; the system is the
+ * paper's A* = M + dt*A divided by dt). M_dev is the matrix of the form
+ * (nu^-1 dev sigma, dev tau), K_div that of (div sigma, div tau) (Section 2.2,
+ * forms M and A; component form Eq. component_form). Each of the d*d tensor
+ * components is a continuous Q1 nodal field on the uniform mesh of [0,1]^d
+ * with n elements per side; every boundary node is eliminated (homogeneous
+ * Dirichlet), leaving m = n-1 interior nodes per axis.
+ *
+ * Solvers: plain CG, and the flexible deflated CG of Algorithm 2 with
+ * deflation space V = (1/sqrt d)(v kron I) (Eq. Vmatrix), whose inner system
+ * V^T A V (a Laplacian, Corollary 1) is solved by the W-cycle multigrid of
+ * Algorithms 3-4 with the RAS smoother of Section 4.2.
+ *
+ * Vector layout (all vectors): node-major. Interior nodes are numbered
+ * lexicographically with x fastest (then y, then z); each node holds its d*d
+ * components in the paper's row-major order [s11 s12 .. s1d s21 .. sdd]
+ * (Section 3.1). Length N = d*d*(n-1)^d doubles. Scalar (inner) vectors have
+ * one double per interior node, same node order.
+ *
+ * Matrix layout: block sparse rows with b x b blocks, b = d*d, one block row
+ * per interior node; block (a, c) is stored for every pair of nodes sharing
+ * an element (3^d neighbourhood clipped at the boundary), columns ascending,
+ * numerical zeros kept; blocks row-major doubles; row_ptr/col_idx int32.
+ *
+ * Ownership: the caller owns every pointer it passes (right-hand sides,
+ * solutions, host arrays); the library never frees them and keeps no
+ * reference after the call returns. The library owns everything inside a
+ * dcg_problem (device memory allocated with cudaMalloc in dcg_assemble /
+ * dcg_setup) and frees it in dcg_destroy.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream). Work is enqueued on it; calls that must read a scalar
+ * back (convergence tests) synchronise that stream.
+ *
+ * Errors: every int-returning call returns a DCG_* status and never throws
+ * across the ABI. On DCG_ERR_CUDA the message of the failing CUDA call is
+ * available from dcg_last_error().
+ */
+#ifndef DCG_H
+#define DCG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define DCG_OK                 0
+#define DCG_ERR_INVALID_ARG    1  /* n < 2, dt <= 0, nu <= 0, tol <= 0, NULL, bad option */
+#define DCG_ERR_NOT_CONVERGED  2  /* max_it reached; x holds the last iterate, stats filled */
+#define DCG_ERR_BREAKDOWN      3  /* (d, M_D d) <= 0 or non-finite; x holds the last iterate */
+#define DCG_ERR_CUDA           4  /* a CUDA call failed; see dcg_last_error() */
+#define DCG_ERR_OOM            5  /* device allocation failed */
+#define DCG_ERR_UNSUPPORTED    6  /* configuration outside what the kernels implement */
+#define DCG_ERR_STATE          7  /* call order violated (e.g. solve before setup) */
+
+/* ---- option values ----------------------------------------------------- */
+#define DCG_INNER_FIXED     0  /* tau_c = c * tol (Eq. fixed_tol, c = c_F) */
+#define DCG_INNER_ADAPTIVE  1  /* tau_c = c * tol ||f|| / ||r_i|| (Eq. tol, c = c_A) */
+#define DCG_INNER_EXACT     2  /* inner system solved directly (fast diagonalisation) */
+
+#define DCG_FCG1     0  /* flexible CG truncated to one direction (m_i = 1) */
+#define DCG_FR       1  /* classical CG coefficients on the deflated system */
+#define DCG_FCG_INF  2  /* untruncated FCG (Algorithm 1), directions stored */
+
+#define DCG_FP64   0  /* everything in FP64 */
+#define DCG_MIXED  1  /* W-cycle (stencils, transfers, RAS) in FP32; outer CG FP64 */
+
+#define DCG_INV_FP32  0  /* RAS patch inverses stored FP32 (mixed mode) */
+#define DCG_INV_BF16  1  /* RAS patch inverses BF16 x FP32 residuals on tensor cores */
+
+#define DCG_RAS_MULTIPLICITY  0  /* D_i = 1/multiplicity (Section 4.2) */
+#define DCG_RAS_RESTRICTED    1  /* D_i = 1 on the core tile, 0 on the overlap */
+
+typedef struct dcg_problem dcg_problem;
+
+/* Uniform mesh of [0,1]^dim with n elements per side. */
+typedef struct {
+  int dim;  /* 2 or 3 */
+  int n;    /* elements per side, >= 2 */
+} dcg_mesh;
+
+/* Solver options (Algorithm 2 inputs m1, m2, tol, n_max; Section 4.2 blocks).
+ * dcg_default_options() fills the defaults given in brackets. */
+typedef struct {
+  int max_levels;    /* multigrid levels incl. the coarsest [4]; coarsen while
+                        n_k is even and n_k >= 8 */
+  int patch;         /* RAS core tile, nodes per axis [4] */
+  int overlap;       /* RAS overlap layers, 2*overlap <= patch [1] */
+  int m1, m2;        /* pre / post smoothing steps [2, 2] */
+  int inner_rule;    /* DCG_INNER_* [FIXED] */
+  double c;          /* c_F or c_A [0.01] */
+  int inner_nmax;    /* W-cycle cap per inner solve, Algorithm 3 n_max [100] */
+  int recurrence;    /* DCG_FCG1 / DCG_FR / DCG_FCG_INF [FCG1] */
+  int precision;     /* DCG_FP64 / DCG_MIXED [FP64] */
+  int ras_inverse;   /* DCG_INV_* (mixed only) [FP32] */
+  int ras_weights;   /* DCG_RAS_* [MULTIPLICITY] */
+  int deflate;       /* 1 = deflated CG, 0 = plain CG [1] */
+  int max_restarts;  /* true-residual restarts after reconstruction [3] */
+  int fcg_max_dirs;  /* FCG(inf): directions kept; 0 = up to max_it [0] */
+  int check_every;   /* outer iterations between host convergence reads [1] */
+} dcg_options;
+
+typedef struct {
+  int status;            /* DCG_* of the solve */
+  int outer_its;         /* outer (F)CG iterations, restarts included */
+  int total_mg_cycles;   /* all W-cycles (paper's "Tot") */
+  int iter_mg_cycles;    /* W-cycles inside outer iterations */
+  int restarts;          /* true-residual restarts */
+  double avg_inner;      /* iter_mg_cycles / outer_its (paper's "Inn") */
+  double true_relres;    /* ||f - A x||_2 / ||f||_2 in FP64 */
+  double solve_ms;       /* wall time of the solve on the stream */
+} dcg_stats;
+
+void dcg_default_options(dcg_options* opts);
+const char* dcg_status_string(int status);
+const char* dcg_last_error(void);
+
+/* Assemble A on the current device (Section 3.1 block structure; forms of
+ * Section 3.2.1 on Q1). nu_elem: NULL for the uniform viscosity `nu`, else a
+ * host array of n^dim per-element viscosities (elements lexicographic, x
+ * fastest), copied during the call. matrix_free = 1 keeps only the element
+ * data and applies A element by element (3D only); 0 stores BSR.
+ * On success *out owns the device data; free with dcg_destroy. */
+int dcg_assemble(const dcg_mesh* mesh, double dt, double nu, const double* nu_elem,
+                 int matrix_free, dcg_problem** out, void* stream);
+
+/* Build the inner hierarchy for `opts`: Z_J = V^T A V (checked on the device
+ * to be the Q1 Laplacian stencil / d), Galerkin coarse stencils
+ * Z_{k-1} = P^T Z_k P (Algorithm 2 setup), RAS patch inverses (Section 4.2)
+ * and the coarsest exact solver. May be called again with new options. */
+int dcg_setup(dcg_problem* p, const dcg_options* opts, void* stream);
+
+/* Solve A x = f to ||f - A x|| <= tol ||f|| (true residual, FP64).
+ * f_dev, x_dev: device arrays of N doubles; x_dev holds the initial guess on
+ * entry and the solution on exit. Returns DCG_OK, DCG_ERR_NOT_CONVERGED or
+ * DCG_ERR_BREAKDOWN (stats filled in all three cases), or an error. */
+int dcg_solve(dcg_problem* p, const double* f_dev, double* x_dev, double tol,
+              int max_it, dcg_stats* stats, void* stream);
+
+/* Same as dcg_solve with host arrays: copies f to the device, solves from
+ * x0 = x_host, copies the solution back into x_host (all on `stream`). */
+int dcg_solve_host(dcg_problem* p, const double* f_host, double* x_host, double tol,
+                   int max_it, dcg_stats* stats, void* stream);
+
+/* Solve nprob problems, each with nrhs right-hand sides, in one call:
+ * f_dev[p*nrhs + r], x_dev[p*nrhs + r] are device arrays of problem p's N.
+ * Problems may differ in n and dt; each must have been set up. The
+ * right-hand sides of one problem advance together (one read of A serves
+ * all of them); converged pairs drop out. stats: nprob*nrhs entries. */
+int dcg_solve_batched(int nprob, dcg_problem* const* probs, int nrhs,
+                      const double* const* f_dev, double* const* x_dev, double tol,
+                      int max_it, dcg_stats* stats, void* stream);
+
+void dcg_destroy(dcg_problem* p);
+
+/* ---- queries and test hooks (same kernels as the solver) --------------- */
+
+/* Sizes: N unknowns, interior nodes, stored blocks, multigrid levels. */
+int dcg_problem_info(const dcg_problem* p, long long* n_unknowns, long long* n_nodes,
+                     long long* nnzb, int* levels);
+
+/* Copy the BSR pattern / values to host arrays of n_nodes+1, nnzb and
+ * nnzb*b*b entries (synchronous). */
+int dcg_export_pattern(const dcg_problem* p, int* row_ptr, int* col_idx);
+int dcg_export_values(const dcg_problem* p, double* values);
+
+/* y = A x (FP64, device arrays of N). */
+int dcg_spmv(const dcg_problem* p, const double* x_dev, double* y_dev, void* stream);
+
+/* q = V^T y (N -> n_nodes) and y = V q (n_nodes -> N), device arrays. */
+int dcg_extract(const dcg_problem* p, const double* y_dev, double* q_dev, void* stream);
+int dcg_embed(const dcg_problem* p, const double* q_dev, double* y_dev, void* stream);
+
+/* Inner operator Z_J z (FP64 stencil of level J, n_nodes in and out). */
+int dcg_inner_apply(const dcg_problem* p, const double* z_dev, double* y_dev, void* stream);
+
+/* Algorithm 3 with a fixed cycle count: z <- z + W-cycle(g - Z_J z) repeated
+ * `ncycles` times (z in/out, FP64, n_nodes), in the precision set up. */
+int dcg_mg_cycles(dcg_problem* p, const double* g_dev, double* z_dev, int ncycles, void* stream);
+
+/* Algorithm 3: cycles until ||g - Z_J z|| <= tol ||g|| or nmax; *ncycles out. */
+int dcg_mg_solve(dcg_problem* p, const double* g_dev, double* z_dev, double tol, int nmax,
+                 int* ncycles, void* stream);
+
+/* One RAS smoothing step on level `level` (1 = coarsest, J = finest) in the
+ * set-up precision: z <- z + S_k (f - Z_k z); FP64 arrays of that level's
+ * node count. */
+int dcg_ras_step(dcg_problem* p, int level, const double* f_dev, double* z_dev, void* stream);
+
+/* Exact coarsest-level solve z = Z_1^-1 f (FP64 arrays of level-1 size). */
+int dcg_coarse_solve(dcg_problem* p, const double* f_dev, double* z_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DCG_H */

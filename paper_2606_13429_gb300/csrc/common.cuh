@@ -1,0 +1,259 @@
+// Common device helpers and the problem object of libdcg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dcg.h"
+
+namespace dcg {
+
+void set_error(const char* what, cudaError_t e);
+void set_error_msg(const std::string& msg);
+
+#define DCG_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e__ = (call);                            \
+    if (e__ != cudaSuccess) {                            \
+      ::dcg::set_error(#call, e__);                      \
+      return e__ == cudaErrorMemoryAllocation ? DCG_ERR_OOM : DCG_ERR_CUDA; \
+    }                                                    \
+  } while (0)
+
+#define DCG_TRY(expr)          \
+  do {                         \
+    int s__ = (expr);          \
+    if (s__ != DCG_OK) return s__; \
+  } while (0)
+
+#define DCG_LAUNCH_CHECK() DCG_CUDA(cudaGetLastError())
+
+constexpr int kMaxDim = 3;
+constexpr int kRedThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions: every CTA writes its partial sums (fixed
+// partition of the index range), the last CTA to finish sums the partials
+// in block order and writes the result; results do not depend on timing.
+// ---------------------------------------------------------------------------
+struct Reduce {
+  double* partials;   // [max_ctas * kMaxVals]
+  unsigned* counter;  // one per reduction slot, zero between launches
+  double* out;        // destination scalars (device)
+};
+constexpr int kMaxVals = 4;
+constexpr int kMaxRedCtas = 65536;
+
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /*[32*NV]*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    v[k] = x;
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) smem[warp * NV + k] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double x = lane < nwarp ? smem[lane * NV + k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[k] = x;
+    }
+  }
+}
+
+// Called by every thread of every CTA after its partials are final.
+// out[k] = sum over CTAs of partial k. Thread 0 of CTA 0..grid-1 contributes.
+template <int NV>
+__device__ __forceinline__ void grid_reduce(double (&v)[NV], const Reduce& r) {
+  __shared__ double smem[32 * NV];
+  __shared__ bool last;
+  block_sum<NV>(v, smem);
+  const unsigned nb = gridDim.x;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) r.partials[(size_t)k * kMaxRedCtas + blockIdx.x] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(r.counter, 1u);
+    last = (t == nb - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double s = 0.0;
+    for (unsigned b = threadIdx.x; b < nb; b += blockDim.x)
+      s += __ldcg(&r.partials[(size_t)k * kMaxRedCtas + b]);
+    acc[k] = s;
+  }
+  block_sum<NV>(acc, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) r.out[k] = acc[k];
+    *r.counter = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Constant 3^d stencil of one multigrid level (index (dx+1) + 3(dy+1) + 9(dz+1)).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Stencil {
+  T c[27];
+};
+
+// RAS tile geometry along one axis of a level.
+struct Tiles1D {
+  int m, P, o, ntile;
+  __host__ __device__ int ext_lo(int t) const { int v = t * P - o; return v < 0 ? 0 : v; }
+  __host__ __device__ int ext_hi(int t) const { int v = (t + 1) * P + o; return v > m ? m : v; }
+  __host__ __device__ int core_lo(int t) const { return t * P; }
+  __host__ __device__ int core_hi(int t) const { int v = (t + 1) * P; return v > m ? m : v; }
+};
+
+struct RasClass {
+  int len[kMaxDim];   // box extent per axis
+  int np;             // prod(len)
+  long long inv_off;  // offset of the inverse in the level's inverse array
+};
+
+struct Level {
+  int n = 0, m = 0;
+  long long nn = 0;                 // m^d nodes
+  Stencil<double> st64{};
+  Stencil<float> st32{};
+  // RAS
+  Tiles1D tiles{};
+  int npatch = 0, nclass = 0, npmax = 0;
+  std::vector<RasClass> classes;
+  int* d_patch_class = nullptr;     // [npatch]
+  long long* d_patch_yoff = nullptr;  // [npatch]
+  int* d_work = nullptr;            // [nwork * 3] (class, first index into d_class_patches, count)
+  int* d_class_patches = nullptr;   // patch ids grouped by class
+  RasClass* d_classes = nullptr;
+  int nwork = 0;
+  long long ylen = 0;
+  void* d_inv = nullptr;            // inverses in the W-cycle precision (row-major, symmetric)
+  void* d_inv_bf16 = nullptr;       // optional BF16 copy
+  // vectors in the W-cycle precision
+  void* f = nullptr;
+  void* z = nullptr;
+  void* y = nullptr;                // RAS patch results
+};
+
+struct Coarse {
+  int m = 0;          // interior nodes per axis on the coarsest level
+  double* S64 = nullptr;   // m x m orthonormal sine matrix
+  float* S32 = nullptr;
+  double* lam64 = nullptr; // eigenvalues of Z_1 (m^d)
+  float* lam32 = nullptr;
+  void* tmp = nullptr;     // work vector (m^d, precision of the cycle)
+};
+
+struct SolverBuffers {
+  double *xh = nullptr, *r = nullptr, *d = nullptr, *q = nullptr, *u = nullptr, *e = nullptr;
+  double *g = nullptr, *zh = nullptr, *zf = nullptr, *rin = nullptr;  // inner FP64 (n_nodes)
+  double* dirs = nullptr;  // FCG(inf): [ndir][N] directions
+  double* qdirs = nullptr; // FCG(inf): [ndir][N] M_D directions
+  double* coef = nullptr;  // FCG(inf): [ndir] coefficients
+  int ndir_cap = 0;
+};
+
+}  // namespace dcg
+
+struct dcg_problem {
+  int dim = 0, n = 0, m = 0, b = 0;
+  long long n_nodes = 0, N = 0, nnzb = 0;
+  double dt = 0, nu = 1;
+  int matrix_free = 0;
+  // BSR (device)
+  int* row_ptr = nullptr;
+  int* col_idx = nullptr;
+  double* vals = nullptr;
+  double* inv_nu_elem = nullptr;   // per-element 1/nu (device, matrix-free or assembly)
+  // scratch for reductions
+  double* partials = nullptr;
+  unsigned* counters = nullptr;    // kNumCounters
+  double* scal = nullptr;          // device scalars
+  double* scal_host = nullptr;     // pinned mirror
+  // setup
+  bool is_setup = false;
+  dcg_options opts{};
+  std::vector<dcg::Level> levels;  // index 0 = coarsest
+  dcg::Coarse coarse;
+  dcg::SolverBuffers sb;
+  double* fine_f64 = nullptr;      // staging for host-array solves (N)
+  double* fine_x64 = nullptr;
+};
+
+namespace dcg {
+
+// device scalar slots
+// Pairs written by one two-value reduction are consecutive:
+// (S_RRN, S_RQ) by the CG update, (S_TMP0, S_TMP1) by the inner residual.
+enum Scal {
+  S_DQ = 0, S_DR, S_RR, S_RRN, S_RQ, S_GG, S_FF, S_TMP0, S_TMP1, S_ALPHA, S_BETA, S_RES,
+  S_COUNT = 16
+};
+constexpr int kNumCounters = 8;
+
+inline Reduce make_reduce(dcg_problem* p, int slot, int counter = 0) {
+  return Reduce{p->partials, p->counters + counter, p->scal + slot};
+}
+
+inline int grid_for(long long n, int threads, int cap = kMaxRedCtas) {
+  long long g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+// launchers implemented in the .cu files
+int assemble_device(dcg_problem* p, const double* nu_elem_host, cudaStream_t s);
+int spmv_plain(dcg_problem* p, const double* x, double* y, cudaStream_t s);
+// y = A x with dot(dv, y) into scal[slot] when dv != nullptr
+int spmv_dot(dcg_problem* p, const double* x, double* y, const double* dv, int slot, cudaStream_t s);
+// y = f - A x, ||y||^2 into scal[slot]
+int spmv_residual(dcg_problem* p, const double* f, const double* x, double* y, int slot, cudaStream_t s);
+// g = V^T A x, ||g||^2 into scal[slot]
+int spmv_vt(dcg_problem* p, const double* x, double* g, int slot, cudaStream_t s);
+// q = A (x - V zh) (zh may be null => x), dot(x, q) into scal[slot]; if x null: q = A (V zh)
+int spmv_defl(dcg_problem* p, const double* x, const double* zh, double* q, int slot, cudaStream_t s);
+// y = f - A(V zh), ||y||^2 into scal[slot]
+int spmv_f_minus_avz(dcg_problem* p, const double* f, const double* zh, double* y, int slot, cudaStream_t s);
+
+// vectors
+int vec_extract(dcg_problem* p, const double* y, double* q, int slot, cudaStream_t s);
+int vec_embed(dcg_problem* p, const double* q, double* y, cudaStream_t s);
+int vec_dot(dcg_problem* p, const double* a, const double* b, long long n, int slot, cudaStream_t s);
+int vec_copy(double* dst, const double* src, long long n, cudaStream_t s);
+int vec_zero(double* dst, long long n, cudaStream_t s);
+
+// solver
+int solve_device(dcg_problem* p, const double* f, double* x, double tol, int max_it, dcg_stats* st, cudaStream_t s);
+int read_scalars(dcg_problem* p, cudaStream_t s);
+
+// multigrid
+int mg_setup(dcg_problem* p, cudaStream_t s);
+void mg_free(dcg_problem* p);
+int mg_inner_apply(dcg_problem* p, const double* z, double* y, cudaStream_t s);
+int mg_cycles(dcg_problem* p, const double* g, double* z, int ncycles, cudaStream_t s);
+int mg_solve(dcg_problem* p, const double* g, double* z, double tol, int nmax, int* ncyc, cudaStream_t s);
+int mg_ras_step_hook(dcg_problem* p, int level, const double* f, double* z, cudaStream_t s);
+int mg_coarse_hook(dcg_problem* p, const double* f, double* z, cudaStream_t s);
+
+}  // namespace dcg

@@ -1,0 +1,1025 @@
+// Multigrid for the inner system Z_J z = g (Algorithms 3 and 4) on the device.
+//
+// Inner matrix: Z_J = V^T A V (Algorithm 2 setup). It is extracted from the
+// assembled A on the device, row by row, and checked to be one constant 3^d
+// stencil (Corollary 1: V^T A V = (1/d) sum_i B_ii, the Q1 Laplacian, with
+// the dt- and nu-dependent mass part cancelling). Levels are therefore
+// applied as constant stencils; coarse stencils come from the Galerkin
+// product Z_{k-1} = P^T Z_k P evaluated on the stencil (Algorithm 2 setup
+// loop; P = nodal bilinear/trilinear interpolation, the natural embedding
+// of nested Q1 spaces, and R = P^T, the reading of Section 4.2's L2
+// projection pair for nested spaces).
+//
+// Smoother (Section 4.2): RAS with boxes = core tiles of P nodes per axis
+// extended by `overlap`, local matrices R_i Z_k R_i^T inverted once per box
+// shape on the device (Gauss-Jordan, FP64), weights 1/multiplicity or 0/1 on
+// the core. One step z <- z + sum_i R_i^T D_i Z_i^-1 R_i (f - Z_k z) is two
+// kernels: (1) per batch of equal-shape boxes: residual on the box,
+// multiplication by the shared inverse (a small dense GEMM), results to a
+// patch-major buffer; (2) per node: weighted sum of the box results.
+//
+// Coarsest level (Algorithm 4, k = 1): exact solve by fast diagonalisation:
+// Z_1 = (1/d) sum_i (x)_ax {K1 if ax = i else M1} with 1D Q1 matrices
+// K1, M1 diagonalised by the orthonormal sine basis S, so
+// Z_1^-1 = (S (x) .. (x) S) Lambda^-1 (S (x) .. (x) S); applied as 2d passes
+// of S along one axis. The coarse Galerkin stencil is checked against that
+// closed form before use.
+//
+// W-cycle recursion (Algorithm 4) runs in the set-up precision (FP32 in
+// mixed mode, FP64 otherwise) and is captured once into a CUDA graph. The
+// driver (Algorithm 3) keeps z and the residual g - Z_J z in FP64 and applies
+// each cycle as a correction: z <- z + W(g - Z_J z, 0), which equals
+// W(g, z) for the affine W-cycle iteration.
+#include "common.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <map>
+
+namespace dcg {
+namespace {
+
+constexpr int kNB = 32;       // boxes per CTA batch in the RAS GEMM
+constexpr int kKC = 32;       // K chunk of the inverse staged in shared memory
+constexpr int kRasThreads = 256;
+constexpr int kMaxNp = 256;   // largest box (nodes) supported
+
+// ---------------------------------------------------------------------------
+// Setup kernels
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
+  // v >= 0: IEEE order equals unsigned integer order
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// rows[a*27 + off] = (V^T A V)[a, a+off]; ref node gets copied by the host.
+template <int D>
+__global__ void k_zj_rows(const int* __restrict__ row_ptr, const int* __restrict__ col_idx,
+                          const double* __restrict__ vals, int m, long long nn, double inv_d,
+                          double* __restrict__ rows, double* __restrict__ maxA) {
+  constexpr int B = D * D;
+  long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (a >= nn) return;
+  double row[27];
+#pragma unroll
+  for (int k = 0; k < 27; ++k) row[k] = 0.0;
+  int ca[3] = {(int)(a % m), (int)((a / m) % m), D > 2 ? (int)(a / ((long long)m * m)) : 0};
+  double mx = 0.0;
+  for (int j = row_ptr[a]; j < row_ptr[a + 1]; ++j) {
+    const long long c = col_idx[j];
+    int cc[3] = {(int)(c % m), (int)((c / m) % m), D > 2 ? (int)(c / ((long long)m * m)) : 0};
+    int o = (cc[0] - ca[0] + 1) + 3 * (cc[1] - ca[1] + 1) + (D > 2 ? 9 * (cc[2] - ca[2] + 1) : 0);
+    const double* blk = vals + (long long)j * B * B;
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        double v = blk[(i * D + i) * B + (l * D + l)];
+        s += v;
+        mx = fmax(mx, fabs(v));
+      }
+    row[o] = s * inv_d;
+  }
+  for (int k = 0; k < 27; ++k) rows[a * 27 + k] = row[k];
+  atomic_max_pos(maxA, mx);
+}
+
+// max over nodes of |row(a) - ref| restricted to neighbours inside the grid
+template <int D>
+__global__ void k_zj_check(const double* __restrict__ rows, const double* __restrict__ ref, int m, long long nn,
+                           double* __restrict__ maxdev) {
+  long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (a >= nn) return;
+  int ca[3] = {(int)(a % m), (int)((a / m) % m), D > 2 ? (int)(a / ((long long)m * m)) : 0};
+  double dev = 0.0;
+  for (int o = 0; o < (D == 2 ? 9 : 27); ++o) {
+    int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+    bool in = true;
+    for (int k = 0; k < D; ++k) in = in && (ca[k] + off[k] >= 0 && ca[k] + off[k] < m);
+    double want = in ? ref[o] : 0.0;
+    dev = fmax(dev, fabs(rows[a * 27 + o] - want));
+  }
+  atomic_max_pos(maxdev, dev);
+}
+
+// Galerkin product on a constant stencil: S_c(D) = sum_{al,be} w(al) w(be) S_f(2D + be - al)
+template <int D>
+__global__ void k_galerkin(const double* __restrict__ sf, double* __restrict__ sc) {
+  int o = threadIdx.x;
+  if (o >= (D == 2 ? 9 : 27)) return;
+  int dl[3] = {o % 3 - 1, (o / 3) % 3 - 1, D > 2 ? o / 9 - 1 : 0};
+  double s = 0.0;
+  for (int ia = 0; ia < (D == 2 ? 9 : 27); ++ia) {
+    int al[3] = {ia % 3 - 1, (ia / 3) % 3 - 1, D > 2 ? ia / 9 - 1 : 0};
+    double wa = 1.0;
+    for (int k = 0; k < D; ++k) wa *= al[k] ? 0.5 : 1.0;
+    for (int ib = 0; ib < (D == 2 ? 9 : 27); ++ib) {
+      int be[3] = {ib % 3 - 1, (ib / 3) % 3 - 1, D > 2 ? ib / 9 - 1 : 0};
+      double wb = 1.0;
+      int so[3];
+      bool in = true;
+      for (int k = 0; k < D; ++k) {
+        wb *= be[k] ? 0.5 : 1.0;
+        so[k] = 2 * dl[k] + be[k] - al[k];
+        in = in && so[k] >= -1 && so[k] <= 1;
+      }
+      if (!in) continue;
+      int si = (so[0] + 1) + 3 * (so[1] + 1) + (D > 2 ? 9 * (so[2] + 1) : 0);
+      s += wa * wb * sf[si];
+    }
+  }
+  sc[o] = s;
+}
+
+// Dense local matrix of a box (np nodes, x fastest) from the stencil.
+template <int D>
+__global__ void k_box_matrix(Stencil<double> st, int lx, int ly, int lz, double* __restrict__ M) {
+  const int np = lx * ly * lz;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)np * np) return;
+  int i = (int)(t / np), j = (int)(t % np);
+  int ci[3] = {i % lx, (i / lx) % ly, i / (lx * ly)};
+  int cj[3] = {j % lx, (j / lx) % ly, j / (lx * ly)};
+  int off[3];
+  bool near = true;
+  for (int k = 0; k < 3; ++k) {
+    off[k] = cj[k] - ci[k];
+    near = near && off[k] >= -1 && off[k] <= 1;
+  }
+  double v = 0.0;
+  if (near) v = st.c[(off[0] + 1) + 3 * (off[1] + 1) + (D > 2 ? 9 * (off[2] + 1) : 0)];
+  M[t] = v;
+}
+
+// In-place Gauss-Jordan inversion of an SPD matrix (no pivoting), one CTA.
+__global__ void k_gauss_jordan(double* __restrict__ a, int n) {
+  extern __shared__ double fcol[];
+  for (int k = 0; k < n; ++k) {
+    const double piv = a[(long long)k * n + k];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) fcol[i] = a[(long long)i * n + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+      a[(long long)k * n + j] = (j == k) ? 1.0 / piv : a[(long long)k * n + j] / piv;
+    __syncthreads();
+    for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) {
+      int i = (int)(t / n), j = (int)(t % n);
+      if (i == k) continue;
+      const double f = fcol[i];
+      if (j == k) a[t] = -f * a[(long long)k * n + k];
+      else a[t] = a[t] - f * a[(long long)k * n + j];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_sym_convert(const double* __restrict__ a, T* __restrict__ out, int n) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  int i = (int)(t / n), j = (int)(t % n);
+  out[t] = (T)(0.5 * (a[t] + a[(long long)j * n + i]));
+}
+
+// sine basis S[i][j] = sqrt(2/(m+1)) sin((i+1)(j+1) pi/(m+1)) and eigenvalues
+template <int D>
+__global__ void k_fdm_setup(int m, double* __restrict__ S, double* __restrict__ lam) {
+  const int n1 = m + 1;
+  const double h = 1.0 / n1;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < (long long)m * m) {
+    int i = (int)(t / m), j = (int)(t % m);
+    long long ij = (long long)(i + 1) * (j + 1) % (2 * n1);
+    S[t] = sqrt(2.0 / n1) * sin(M_PI * (double)ij / n1);
+  }
+  long long nn = 1;
+  for (int k = 0; k < D; ++k) nn *= m;
+  if (t < nn) {
+    int jj[3] = {(int)(t % m), (int)((t / m) % m), D > 2 ? (int)(t / ((long long)m * m)) : 0};
+    double kap[3], mu[3];
+    for (int k = 0; k < D; ++k) {
+      double th = M_PI * (jj[k] + 1) / n1;
+      kap[k] = (2.0 / h) * (1.0 - cos(th));
+      mu[k] = (h / 3.0) * (2.0 + cos(th));
+    }
+    double l = 0.0;
+    for (int i = 0; i < D; ++i) {
+      double term = kap[i];
+      for (int k = 0; k < D; ++k)
+        if (k != i) term *= mu[k];
+      l += term;
+    }
+    lam[t] = l / D;
+  }
+}
+
+template <typename T>
+__global__ void k_to_t(const double* __restrict__ a, T* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (T)a[i];
+}
+
+// ---------------------------------------------------------------------------
+// W-cycle kernels
+// ---------------------------------------------------------------------------
+
+template <int D>
+__device__ __forceinline__ void coords_of(long long a, int m, int (&c)[3]) {
+  c[0] = (int)(a % m);
+  c[1] = (int)((a / m) % m);
+  c[2] = D > 2 ? (int)(a / ((long long)m * m)) : 0;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ T stencil_apply(const Stencil<T>& st, const T* __restrict__ z, int m, const int (&c)[3]) {
+  T acc = 0;
+  const long long mm = (long long)m * m;
+#pragma unroll
+  for (int dz = (D > 2 ? -1 : 0); dz <= (D > 2 ? 1 : 0); ++dz) {
+    const int zc = c[2] + dz;
+    if (D > 2 && (zc < 0 || zc >= m)) continue;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yc = c[1] + dy;
+      if (yc < 0 || yc >= m) continue;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int xc = c[0] + dx;
+        if (xc < 0 || xc >= m) continue;
+        const T w = st.c[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+        acc += w * z[xc + (long long)m * yc + (D > 2 ? mm * zc : 0)];
+      }
+    }
+  }
+  return acc;
+}
+
+// y = f - Z z
+template <typename T, int D>
+__global__ void k_apply(Stencil<T> st, const T* __restrict__ z, T* __restrict__ y, int m, long long nn) {
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nn; a += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    coords_of<D>(a, m, c);
+    y[a] = stencil_apply<T, D>(st, z, m, c);
+  }
+}
+
+template <typename T, int D>
+__global__ void k_residual(Stencil<T> st, const T* __restrict__ f, const T* __restrict__ z, T* __restrict__ y, int m,
+                           long long nn) {
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nn; a += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    coords_of<D>(a, m, c);
+    y[a] = f[a] - stencil_apply<T, D>(st, z, m, c);
+  }
+}
+
+// coarse[I] = sum_al w(al) fine[2I+1+al]  (P^T)
+template <typename T, int D>
+__global__ void k_restrict(const T* __restrict__ fine, T* __restrict__ coarse, int mf, int mc, long long nc) {
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < nc; I += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    coords_of<D>(I, mc, c);
+    T acc = 0;
+    for (int az = (D > 2 ? -1 : 0); az <= (D > 2 ? 1 : 0); ++az)
+      for (int ay = -1; ay <= 1; ++ay)
+        for (int ax = -1; ax <= 1; ++ax) {
+          const int fx = 2 * c[0] + 1 + ax, fy = 2 * c[1] + 1 + ay, fz = D > 2 ? 2 * c[2] + 1 + az : 0;
+          const T w = (T)((ax ? 0.5 : 1.0) * (ay ? 0.5 : 1.0) * (az ? 0.5 : 1.0));
+          acc += w * fine[fx + (long long)mf * fy + (long long)mf * mf * fz];
+        }
+    coarse[I] = acc;
+  }
+}
+
+// fine[a] += sum_I P[a][I] coarse[I]
+template <typename T, int D>
+__global__ void k_prolong_add(const T* __restrict__ coarse, T* __restrict__ fine, int mf, int mc, long long nf) {
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nf; a += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    coords_of<D>(a, mf, c);
+    int lo[3], cnt[3];
+    T w0[3], w1[3];
+    for (int k = 0; k < 3; ++k) {
+      if (k >= D) { lo[k] = 0; cnt[k] = 1; w0[k] = 1; w1[k] = 0; continue; }
+      if (c[k] & 1) { lo[k] = (c[k] - 1) >> 1; cnt[k] = 1; w0[k] = 1; w1[k] = 0; }
+      else { lo[k] = (c[k] >> 1) - 1; cnt[k] = 2; w0[k] = (T)0.5; w1[k] = (T)0.5; }
+    }
+    T acc = 0;
+    for (int iz = 0; iz < cnt[2]; ++iz)
+      for (int iy = 0; iy < cnt[1]; ++iy)
+        for (int ix = 0; ix < cnt[0]; ++ix) {
+          const int X = lo[0] + ix, Y = lo[1] + iy, Z = lo[2] + iz;
+          if (X < 0 || X >= mc || Y < 0 || Y >= mc || (D > 2 && (Z < 0 || Z >= mc))) continue;
+          const T w = (ix ? w1[0] : w0[0]) * (iy ? w1[1] : w0[1]) * (iz ? w1[2] : w0[2]);
+          acc += w * coarse[X + (long long)mc * Y + (long long)mc * mc * Z];
+        }
+    fine[a] += acc;
+  }
+}
+
+struct RasArgs {
+  int m, ntile, P, o;
+  const int* work;           // [nwork*3]
+  const int* class_patches;  // grouped patch ids
+  const RasClass* classes;
+  const long long* yoff;     // [npatch]
+  int nwork;
+};
+
+// (1) residual on each box of a batch, times the shared inverse, to y.
+template <typename T, int D>
+__global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, Stencil<T> st, const T* __restrict__ f,
+                                                            const T* __restrict__ z, const T* __restrict__ inv,
+                                                            T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* G = reinterpret_cast<T*>(smem_raw);            // [npmax][kNB]
+  const int tid = threadIdx.x;
+  const int tx = tid & 7;   // patch group (4 patches each)
+  const int ty = tid >> 3;  // row group
+  const Tiles1D tl{ra.m, ra.P, ra.o, ra.ntile};
+  for (int w = blockIdx.x; w < ra.nwork; w += gridDim.x) {
+    const int cls = ra.work[3 * w], first = ra.work[3 * w + 1], nb = ra.work[3 * w + 2];
+    const RasClass C = ra.classes[cls];
+    const int np = C.np;
+    T* As = G + (size_t)np * kNB;                    // [kKC][np]
+    __syncthreads();
+    // gather residuals: patch fastest
+    for (int idx = tid; idx < np * kNB; idx += blockDim.x) {
+      const int b = idx % kNB, k = idx / kNB;
+      T r = 0;
+      if (b < nb) {
+        const int pid = ra.class_patches[first + b];
+        int t3[3] = {pid % ra.ntile, (pid / ra.ntile) % ra.ntile, D > 2 ? pid / (ra.ntile * ra.ntile) : 0};
+        int lk[3] = {k % C.len[0], (k / C.len[0]) % C.len[1], D > 2 ? k / (C.len[0] * C.len[1]) : 0};
+        int c[3];
+        for (int q = 0; q < 3; ++q) c[q] = (q < D) ? tl.ext_lo(t3[q]) + lk[q] : 0;
+        const long long a = c[0] + (long long)ra.m * c[1] + (D > 2 ? (long long)ra.m * ra.m * c[2] : 0);
+        r = f[a] - stencil_apply<T, D>(st, z, ra.m, c);
+      }
+      G[(size_t)k * kNB + b] = r;
+    }
+    // GEMM: Y[i][b] = sum_k inv[i][k] G[k][b]; inv symmetric, row k = column k
+    constexpr int RI = kMaxNp / 32;
+    T acc[RI][4];
+#pragma unroll
+    for (int r = 0; r < RI; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = 0;
+    const T* invc = inv + C.inv_off;
+    for (int k0 = 0; k0 < np; k0 += kKC) {
+      const int kc = min(kKC, np - k0);
+      __syncthreads();
+      for (int idx = tid; idx < kc * np; idx += blockDim.x) As[idx] = invc[(size_t)k0 * np + idx];
+      __syncthreads();
+      for (int kk = 0; kk < kc; ++kk) {
+        const T* g = G + (size_t)(k0 + kk) * kNB + 4 * tx;
+        const T g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3];
+        const T* arow = As + (size_t)kk * np;
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+          const int i = ty + 32 * r;
+          if (i < np) {
+            const T av = arow[i];
+            acc[r][0] += av * g0;
+            acc[r][1] += av * g1;
+            acc[r][2] += av * g2;
+            acc[r][3] += av * g3;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int b = 4 * tx + c;
+      if (b >= nb) continue;
+      const int pid = ra.class_patches[first + b];
+      T* yp = y + ra.yoff[pid];
+#pragma unroll
+      for (int r = 0; r < RI; ++r) {
+        const int i = ty + 32 * r;
+        if (i < np) yp[i] = acc[r][c];
+      }
+    }
+  }
+}
+
+// (2) z[j] += D_j * sum over boxes containing j of y_box[local(j)]
+template <typename T, int D>
+__global__ void k_ras_update(RasArgs ra, const T* __restrict__ y, T* __restrict__ z, long long nn, int restricted) {
+  const Tiles1D tl{ra.m, ra.P, ra.o, ra.ntile};
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nn; a += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    coords_of<D>(a, ra.m, c);
+    int tlist[3][3], nt[3];
+    for (int q = 0; q < 3; ++q) {
+      nt[q] = 0;
+      if (q >= D) { tlist[q][0] = 0; nt[q] = 1; continue; }
+      const int t0 = c[q] / ra.P;
+      for (int t = t0 - 1; t <= t0 + 1; ++t) {
+        if (t < 0 || t >= ra.ntile) continue;
+        if (restricted && t != t0) continue;
+        if (c[q] >= tl.ext_lo(t) && c[q] < tl.ext_hi(t)) tlist[q][nt[q]++] = t;
+      }
+    }
+    T s = 0;
+    for (int iz = 0; iz < nt[2]; ++iz)
+      for (int iy = 0; iy < nt[1]; ++iy)
+        for (int ix = 0; ix < nt[0]; ++ix) {
+          const int tx = tlist[0][ix], ty = tlist[1][iy], tz = tlist[2][iz];
+          const int pid = tx + ra.ntile * (ty + (D > 2 ? ra.ntile * tz : 0));
+          const int lx = c[0] - tl.ext_lo(tx), ly = c[1] - tl.ext_lo(ty);
+          const int Lx = tl.ext_hi(tx) - tl.ext_lo(tx), Ly = tl.ext_hi(ty) - tl.ext_lo(ty);
+          const int lz = D > 2 ? c[2] - tl.ext_lo(tz) : 0;
+          s += y[ra.yoff[pid] + lx + (long long)Lx * (ly + (long long)Ly * lz)];
+        }
+    const int mult = nt[0] * nt[1] * nt[2];
+    z[a] += restricted ? s : s / (T)mult;
+  }
+}
+
+// out[line, i] = sum_j S[i][j] in[line, j] along `axis`; optional divide by lam
+template <typename T, int D>
+__global__ void k_fdm_pass(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ S,
+                           const T* __restrict__ lam, int m, int axis, long long nn) {
+  long long stride = 1;
+  for (int k = 0; k < axis; ++k) stride *= m;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)((t / stride) % m);
+    const long long base = t - (long long)i * stride;
+    T acc = 0;
+    const T* Si = S + (size_t)i * m;
+    for (int j = 0; j < m; ++j) acc += Si[j] * in[base + (long long)j * stride];
+    out[t] = lam ? acc / lam[t] : acc;
+  }
+}
+
+// FP64 fine residual r = g - Z_J z, stored into the cycle's level-J RHS (in
+// the cycle precision); zeroes the level-J iterate; reduces ||r||^2, ||g||^2.
+template <typename T, int D>
+__global__ void k_inner_residual(Stencil<double> st, const double* __restrict__ g, const double* __restrict__ z,
+                                 T* __restrict__ fJ, T* __restrict__ zJ, double* __restrict__ r64, int m, long long nn,
+                                 Reduce red) {
+  double part[2] = {0.0, 0.0};
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nn; a += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    coords_of<D>(a, m, c);
+    const double ga = g[a];
+    const double r = ga - stencil_apply<double, D>(st, z, m, c);
+    if (fJ) fJ[a] = (T)r;
+    if (zJ) zJ[a] = (T)0;
+    if (r64) r64[a] = r;
+    part[0] = fma(r, r, part[0]);
+    part[1] = fma(ga, ga, part[1]);
+  }
+  grid_reduce<2>(part, red);
+}
+
+template <typename T>
+__global__ void k_accumulate(double* __restrict__ z, const T* __restrict__ c, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] += (double)c[i];
+}
+
+template <typename T>
+__global__ void k_from_t(const T* __restrict__ a, double* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+struct MGState {
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t wexec = nullptr;
+  bool fp32 = false;
+};
+std::map<const dcg_problem*, MGState> g_state;
+
+std::vector<int> level_sizes(int n, int max_levels) {
+  std::vector<int> s{n};
+  while (s.back() % 2 == 0 && s.back() >= 8 && (int)s.size() < max_levels) s.push_back(s.back() / 2);
+  return s;
+}
+
+long long ipow(int b, int e) {
+  long long r = 1;
+  for (int k = 0; k < e; ++k) r *= b;
+  return r;
+}
+
+// closed-form Q1 Laplacian stencil / d at spacing h (reference for the FDM solver)
+Stencil<double> q1_laplacian_over_d(int D, double h) {
+  Stencil<double> st{};
+  const double K[3] = {-1.0 / h, 2.0 / h, -1.0 / h};
+  const double M[3] = {h / 6.0, 4.0 * h / 6.0, h / 6.0};
+  for (int o = 0; o < 27; ++o) {
+    int off[3] = {o % 3, (o / 3) % 3, o / 9};
+    if (D == 2 && off[2] != 1) continue;
+    double s = 0.0;
+    for (int i = 0; i < D; ++i) {
+      double term = 1.0;
+      for (int k = 0; k < D; ++k) term *= (k == i) ? K[off[k]] : M[off[k]];
+      s += term;
+    }
+    int idx = off[0] + 3 * off[1] + (D == 2 ? 0 : 9 * off[2]);
+    st.c[idx] = s / D;
+  }
+  return st;
+}
+
+template <typename T>
+size_t ras_smem_bytes(int npmax) {
+  return sizeof(T) * ((size_t)npmax * kNB + (size_t)kKC * npmax);
+}
+
+void free_level(Level& L) {
+  cudaFree(L.d_patch_class); cudaFree(L.d_patch_yoff); cudaFree(L.d_work); cudaFree(L.d_class_patches);
+  cudaFree(L.d_classes); cudaFree(L.d_inv); cudaFree(L.d_inv_bf16); cudaFree(L.f); cudaFree(L.z); cudaFree(L.y);
+  L = Level{};
+}
+
+int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
+  const int D = p->dim;
+  const dcg_options& o = p->opts;
+  L.tiles = Tiles1D{L.m, o.patch, o.overlap, (L.m + o.patch - 1) / o.patch};
+  const int nt = L.tiles.ntile;
+  L.npatch = (int)ipow(nt, D);
+  // per-axis extent of every tile
+  std::vector<int> len1(nt);
+  for (int t = 0; t < nt; ++t) len1[t] = L.tiles.ext_hi(t) - L.tiles.ext_lo(t);
+  std::map<std::vector<int>, int> cls_of;
+  std::vector<int> pclass(L.npatch);
+  std::vector<long long> yoff(L.npatch);
+  long long y = 0;
+  L.classes.clear();
+  for (int pid = 0; pid < L.npatch; ++pid) {
+    int t3[3] = {pid % nt, (pid / nt) % nt, D > 2 ? pid / (nt * nt) : 0};
+    std::vector<int> key(3, 1);
+    for (int k = 0; k < D; ++k) key[k] = len1[t3[k]];
+    auto it = cls_of.find(key);
+    int c;
+    if (it == cls_of.end()) {
+      c = (int)L.classes.size();
+      cls_of[key] = c;
+      RasClass rc{};
+      rc.len[0] = key[0]; rc.len[1] = key[1]; rc.len[2] = key[2];
+      rc.np = key[0] * key[1] * key[2];
+      L.classes.push_back(rc);
+    } else {
+      c = it->second;
+    }
+    pclass[pid] = c;
+    yoff[pid] = y;
+    y += L.classes[c].np;
+  }
+  L.ylen = y < L.nn ? L.nn : y;
+  L.nclass = (int)L.classes.size();
+  L.npmax = 0;
+  long long inv_total = 0;
+  for (auto& c : L.classes) {
+    if (c.np > kMaxNp) {
+      set_error_msg("RAS box larger than 256 nodes: reduce patch/overlap");
+      return DCG_ERR_UNSUPPORTED;
+    }
+    c.inv_off = inv_total;
+    inv_total += (long long)c.np * c.np;
+    L.npmax = std::max(L.npmax, c.np);
+  }
+  // group patches by class, batch into work items
+  std::vector<int> grouped;
+  std::vector<int> work;
+  for (int c = 0; c < L.nclass; ++c) {
+    int start = (int)grouped.size();
+    for (int pid = 0; pid < L.npatch; ++pid)
+      if (pclass[pid] == c) grouped.push_back(pid);
+    int cnt = (int)grouped.size() - start;
+    for (int b = 0; b < cnt; b += kNB) {
+      work.push_back(c);
+      work.push_back(start + b);
+      work.push_back(std::min(kNB, cnt - b));
+    }
+  }
+  L.nwork = (int)work.size() / 3;
+  DCG_CUDA(cudaMalloc(&L.d_patch_class, sizeof(int) * L.npatch));
+  DCG_CUDA(cudaMalloc(&L.d_patch_yoff, sizeof(long long) * L.npatch));
+  DCG_CUDA(cudaMalloc(&L.d_class_patches, sizeof(int) * grouped.size()));
+  DCG_CUDA(cudaMalloc(&L.d_work, sizeof(int) * work.size()));
+  DCG_CUDA(cudaMalloc(&L.d_classes, sizeof(RasClass) * L.nclass));
+  DCG_CUDA(cudaMemcpyAsync(L.d_patch_class, pclass.data(), sizeof(int) * L.npatch, cudaMemcpyHostToDevice, s));
+  DCG_CUDA(cudaMemcpyAsync(L.d_patch_yoff, yoff.data(), sizeof(long long) * L.npatch, cudaMemcpyHostToDevice, s));
+  DCG_CUDA(cudaMemcpyAsync(L.d_class_patches, grouped.data(), sizeof(int) * grouped.size(), cudaMemcpyHostToDevice, s));
+  DCG_CUDA(cudaMemcpyAsync(L.d_work, work.data(), sizeof(int) * work.size(), cudaMemcpyHostToDevice, s));
+  DCG_CUDA(cudaMemcpyAsync(L.d_classes, L.classes.data(), sizeof(RasClass) * L.nclass, cudaMemcpyHostToDevice, s));
+  // local inverses: box matrix from the stencil, Gauss-Jordan in FP64
+  const size_t tsz = fp32 ? sizeof(float) : sizeof(double);
+  DCG_CUDA(cudaMalloc(&L.d_inv, tsz * inv_total));
+  double* work64 = nullptr;
+  DCG_CUDA(cudaMalloc(&work64, sizeof(double) * (size_t)L.npmax * L.npmax));
+  for (auto& c : L.classes) {
+    const int np = c.np;
+    const long long nel = (long long)np * np;
+    const int g = (int)((nel + 255) / 256);
+    if (D == 2) k_box_matrix<2><<<g, 256, 0, s>>>(L.st64, c.len[0], c.len[1], 1, work64);
+    else k_box_matrix<3><<<g, 256, 0, s>>>(L.st64, c.len[0], c.len[1], c.len[2], work64);
+    DCG_LAUNCH_CHECK();
+    k_gauss_jordan<<<1, 1024, sizeof(double) * np, s>>>(work64, np);
+    DCG_LAUNCH_CHECK();
+    if (fp32) k_sym_convert<float><<<g, 256, 0, s>>>(work64, (float*)L.d_inv + c.inv_off, np);
+    else k_sym_convert<double><<<g, 256, 0, s>>>(work64, (double*)L.d_inv + c.inv_off, np);
+    DCG_LAUNCH_CHECK();
+  }
+  DCG_CUDA(cudaStreamSynchronize(s));
+  cudaFree(work64);
+  DCG_CUDA(cudaMalloc(&L.y, tsz * L.ylen));
+  return DCG_OK;
+}
+
+template <typename T>
+Stencil<T> st_of(const Level& L);
+template <>
+Stencil<float> st_of<float>(const Level& L) { return L.st32; }
+template <>
+Stencil<double> st_of<double>(const Level& L) { return L.st64; }
+
+template <typename T>
+const T* coarse_S(const Coarse& c);
+template <>
+const float* coarse_S<float>(const Coarse& c) { return c.S32; }
+template <>
+const double* coarse_S<double>(const Coarse& c) { return c.S64; }
+template <typename T>
+const T* coarse_lam(const Coarse& c);
+template <>
+const float* coarse_lam<float>(const Coarse& c) { return c.lam32; }
+template <>
+const double* coarse_lam<double>(const Coarse& c) { return c.lam64; }
+
+template <typename T, int D>
+int coarse_solve_t(dcg_problem* p, const T* f, T* z, cudaStream_t s) {
+  const Coarse& C = p->coarse;
+  const long long nn = ipow(C.m, D);
+  T* tmp = (T*)C.tmp;
+  const T* S = coarse_S<T>(C);
+  const T* lam = coarse_lam<T>(C);
+  const int g = grid_for(nn, 256, 4096);
+  if (D == 2) {
+    k_fdm_pass<T, D><<<g, 256, 0, s>>>(f, tmp, S, nullptr, C.m, 0, nn);
+    k_fdm_pass<T, D><<<g, 256, 0, s>>>(tmp, z, S, lam, C.m, 1, nn);
+    k_fdm_pass<T, D><<<g, 256, 0, s>>>(z, tmp, S, nullptr, C.m, 1, nn);
+    k_fdm_pass<T, D><<<g, 256, 0, s>>>(tmp, z, S, nullptr, C.m, 0, nn);
+  } else {
+    k_fdm_pass<T, D><<<g, 256, 0, s>>>(f, tmp, S, nullptr, C.m, 0, nn);
+    k_fdm_pass<T, D><<<g, 256, 0, s>>>(tmp, z, S, nullptr, C.m, 1, nn);
+    k_fdm_pass<T, D><<<g, 256, 0, s>>>(z, tmp, S, lam, C.m, 2, nn);
+    k_fdm_pass<T, D><<<g, 256, 0, s>>>(tmp, z, S, nullptr, C.m, 2, nn);
+    k_fdm_pass<T, D><<<g, 256, 0, s>>>(z, tmp, S, nullptr, C.m, 1, nn);
+    k_fdm_pass<T, D><<<g, 256, 0, s>>>(tmp, z, S, nullptr, C.m, 0, nn);
+  }
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
+
+template <typename T, int D>
+int ras_step_t(dcg_problem* p, Level& L, cudaStream_t s) {
+  RasArgs ra{};
+  ra.m = L.m; ra.ntile = L.tiles.ntile; ra.P = L.tiles.P; ra.o = L.tiles.o;
+  ra.work = L.d_work; ra.class_patches = L.d_class_patches; ra.classes = L.d_classes; ra.yoff = L.d_patch_yoff;
+  ra.nwork = L.nwork;
+  const size_t smem = ras_smem_bytes<T>(L.npmax);
+  int grid = std::min(L.nwork, 152 * 4);
+  k_ras_solve<T, D><<<grid, kRasThreads, smem, s>>>(ra, st_of<T>(L), (const T*)L.f, (const T*)L.z,
+                                                    (const T*)L.d_inv, (T*)L.y);
+  DCG_LAUNCH_CHECK();
+  k_ras_update<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(ra, (const T*)L.y, (T*)L.z, L.nn,
+                                                                p->opts.ras_weights == DCG_RAS_RESTRICTED);
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
+
+template <typename T, int D>
+int wcycle_t(dcg_problem* p, int k, cudaStream_t s) {
+  Level& L = p->levels[k - 1];
+  if (k == 1) return coarse_solve_t<T, D>(p, (const T*)L.f, (T*)L.z, s);
+  Level& Lc = p->levels[k - 2];
+  for (int i = 0; i < p->opts.m1; ++i) DCG_TRY((ras_step_t<T, D>(p, L, s)));
+  k_residual<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(st_of<T>(L), (const T*)L.f, (const T*)L.z, (T*)L.y, L.m,
+                                                             L.nn);
+  DCG_LAUNCH_CHECK();
+  k_restrict<T, D><<<grid_for(Lc.nn, 256, 8192), 256, 0, s>>>((const T*)L.y, (T*)Lc.f, L.m, Lc.m, Lc.nn);
+  DCG_LAUNCH_CHECK();
+  DCG_CUDA(cudaMemsetAsync(Lc.z, 0, sizeof(T) * Lc.nn, s));
+  DCG_TRY((wcycle_t<T, D>(p, k - 1, s)));
+  DCG_TRY((wcycle_t<T, D>(p, k - 1, s)));
+  k_prolong_add<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>((const T*)Lc.z, (T*)L.z, L.m, Lc.m, L.nn);
+  DCG_LAUNCH_CHECK();
+  for (int i = 0; i < p->opts.m2; ++i) DCG_TRY((ras_step_t<T, D>(p, L, s)));
+  return DCG_OK;
+}
+
+template <typename T>
+int wcycle_dispatch(dcg_problem* p, cudaStream_t s) {
+  const int J = (int)p->levels.size();
+  return p->dim == 2 ? wcycle_t<T, 2>(p, J, s) : wcycle_t<T, 3>(p, J, s);
+}
+
+int build_wcycle_graph(dcg_problem* p) {
+  MGState& S = g_state[p];
+  if (S.wexec) { cudaGraphExecDestroy(S.wexec); S.wexec = nullptr; }
+  if (!S.cap) DCG_CUDA(cudaStreamCreateWithFlags(&S.cap, cudaStreamNonBlocking));
+  DCG_CUDA(cudaStreamBeginCapture(S.cap, cudaStreamCaptureModeThreadLocal));
+  int st = S.fp32 ? wcycle_dispatch<float>(p, S.cap) : wcycle_dispatch<double>(p, S.cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(S.cap, &graph);
+  if (st != DCG_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+  if (e != cudaSuccess) { set_error("cudaStreamEndCapture", e); return DCG_ERR_CUDA; }
+  e = cudaGraphInstantiate(&S.wexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) { set_error("cudaGraphInstantiate", e); return DCG_ERR_CUDA; }
+  return DCG_OK;
+}
+
+int run_wcycle(dcg_problem* p, cudaStream_t s) {
+  MGState& S = g_state[p];
+  if (!S.wexec) DCG_TRY(build_wcycle_graph(p));
+  DCG_CUDA(cudaGraphLaunch(S.wexec, s));
+  return DCG_OK;
+}
+
+bool exact_mode(const dcg_problem* p) { return p->opts.inner_rule == DCG_INNER_EXACT; }
+
+}  // namespace
+
+void mg_free(dcg_problem* p) {
+  for (auto& L : p->levels) free_level(L);
+  p->levels.clear();
+  cudaFree(p->coarse.S64); cudaFree(p->coarse.S32); cudaFree(p->coarse.lam64); cudaFree(p->coarse.lam32);
+  cudaFree(p->coarse.tmp);
+  p->coarse = Coarse{};
+  auto it = g_state.find(p);
+  if (it != g_state.end()) {
+    if (it->second.wexec) cudaGraphExecDestroy(it->second.wexec);
+    if (it->second.cap) cudaStreamDestroy(it->second.cap);
+    g_state.erase(it);
+  }
+}
+
+int mg_setup(dcg_problem* p, cudaStream_t s) {
+  mg_free(p);
+  const int D = p->dim;
+  const dcg_options& o = p->opts;
+  const bool fp32 = (o.precision == DCG_MIXED) && !exact_mode(p);
+  if (p->matrix_free) {
+    set_error_msg("inner hierarchy for matrix-free problems is built by the matrix-free module");
+    return DCG_ERR_UNSUPPORTED;
+  }
+  // --- Z_J = V^T A V from the assembled matrix, checked to be one stencil
+  double* rows = nullptr;
+  double* scal2 = nullptr;
+  DCG_CUDA(cudaMalloc(&rows, sizeof(double) * 27 * p->n_nodes));
+  DCG_CUDA(cudaMalloc(&scal2, sizeof(double) * 2 + sizeof(double) * 27 * 2));
+  DCG_CUDA(cudaMemsetAsync(scal2, 0, sizeof(double) * 2, s));
+  const int g = grid_for(p->n_nodes, 256, 1 << 30);
+  if (D == 2) k_zj_rows<2><<<g, 256, 0, s>>>(p->row_ptr, p->col_idx, p->vals, p->m, p->n_nodes, 1.0 / D, rows, scal2);
+  else k_zj_rows<3><<<g, 256, 0, s>>>(p->row_ptr, p->col_idx, p->vals, p->m, p->n_nodes, 1.0 / D, rows, scal2);
+  DCG_LAUNCH_CHECK();
+  const int mid = p->m / 2;
+  const long long ref = mid + (long long)p->m * mid + (D > 2 ? (long long)p->m * p->m * mid : 0);
+  double* d_ref = scal2 + 2;
+  DCG_CUDA(cudaMemcpyAsync(d_ref, rows + ref * 27, sizeof(double) * 27, cudaMemcpyDeviceToDevice, s));
+  if (D == 2) k_zj_check<2><<<g, 256, 0, s>>>(rows, d_ref, p->m, p->n_nodes, scal2 + 1);
+  else k_zj_check<3><<<g, 256, 0, s>>>(rows, d_ref, p->m, p->n_nodes, scal2 + 1);
+  DCG_LAUNCH_CHECK();
+  double h_sc[2];
+  Stencil<double> stJ{};
+  DCG_CUDA(cudaMemcpyAsync(h_sc, scal2, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+  DCG_CUDA(cudaMemcpyAsync(stJ.c, d_ref, sizeof(double) * 27, cudaMemcpyDeviceToHost, s));
+  DCG_CUDA(cudaStreamSynchronize(s));
+  cudaFree(rows);
+  double smax = 0.0;
+  for (double v : stJ.c) smax = std::max(smax, std::fabs(v));
+  const double tol = std::max(1e-12 * smax, 8.0 * D * D * std::ldexp(1.0, -52) * h_sc[0]);
+  if (!(h_sc[1] <= tol) || p->m < 1) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "V^T A V is not a constant stencil (deviation %.3e, tolerance %.3e)", h_sc[1], tol);
+    set_error_msg(buf);
+    cudaFree(scal2);
+    return DCG_ERR_UNSUPPORTED;
+  }
+  // --- levels
+  std::vector<int> sizes = exact_mode(p) ? std::vector<int>{p->n} : level_sizes(p->n, o.max_levels);
+  const int J = (int)sizes.size();
+  p->levels.assign(J, Level{});
+  {
+    Level& LJ = p->levels[J - 1];
+    LJ.n = sizes[0];
+    LJ.m = sizes[0] - 1;
+    LJ.nn = ipow(LJ.m, D);
+    LJ.st64 = stJ;
+  }
+  double* d_sf = scal2 + 2;
+  double* d_sc = scal2 + 2 + 27;
+  for (int k = J - 1; k >= 1; --k) {
+    Level& Lf = p->levels[k];
+    Level& Lc = p->levels[k - 1];
+    Lc.n = sizes[J - k];
+    Lc.m = Lc.n - 1;
+    Lc.nn = ipow(Lc.m, D);
+    DCG_CUDA(cudaMemcpyAsync(d_sf, Lf.st64.c, sizeof(double) * 27, cudaMemcpyHostToDevice, s));
+    DCG_CUDA(cudaMemsetAsync(d_sc, 0, sizeof(double) * 27, s));
+    if (D == 2) k_galerkin<2><<<1, 32, 0, s>>>(d_sf, d_sc);
+    else k_galerkin<3><<<1, 32, 0, s>>>(d_sf, d_sc);
+    DCG_LAUNCH_CHECK();
+    DCG_CUDA(cudaMemcpyAsync(Lc.st64.c, d_sc, sizeof(double) * 27, cudaMemcpyDeviceToHost, s));
+    DCG_CUDA(cudaStreamSynchronize(s));
+  }
+  cudaFree(scal2);
+  for (auto& L : p->levels)
+    for (int k = 0; k < 27; ++k) L.st32.c[k] = (float)L.st64.c[k];
+  // coarsest: check the closed form the fast-diagonalisation solver assumes
+  {
+    Level& L1 = p->levels[0];
+    Stencil<double> cf = q1_laplacian_over_d(D, 1.0 / L1.n);
+    double dev = 0.0, mx = 0.0;
+    for (int k = 0; k < 27; ++k) {
+      dev = std::max(dev, std::fabs(cf.c[k] - L1.st64.c[k]));
+      mx = std::max(mx, std::fabs(cf.c[k]));
+    }
+    if (!(dev <= 1e-10 * mx)) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "coarsest stencil is not the Q1 Laplacian (deviation %.3e)", dev);
+      set_error_msg(buf);
+      return DCG_ERR_UNSUPPORTED;
+    }
+  }
+  // --- buffers and RAS
+  const size_t tsz = fp32 ? sizeof(float) : sizeof(double);
+  g_state[p].fp32 = fp32;
+  for (int k = 0; k < J; ++k) {
+    Level& L = p->levels[k];
+    DCG_CUDA(cudaMalloc(&L.f, tsz * L.nn));
+    DCG_CUDA(cudaMalloc(&L.z, tsz * L.nn));
+    DCG_CUDA(cudaMemsetAsync(L.z, 0, tsz * L.nn, s));
+    if (k >= 1) DCG_TRY(setup_ras(p, L, fp32, s));
+  }
+  // --- coarsest solver
+  {
+    Coarse& C = p->coarse;
+    C.m = p->levels[0].m;
+    const long long nn = p->levels[0].nn;
+    DCG_CUDA(cudaMalloc(&C.S64, sizeof(double) * C.m * C.m));
+    DCG_CUDA(cudaMalloc(&C.lam64, sizeof(double) * nn));
+    DCG_CUDA(cudaMalloc(&C.tmp, tsz * nn));
+    long long work = std::max<long long>((long long)C.m * C.m, nn);
+    int gg = (int)((work + 255) / 256);
+    if (D == 2) k_fdm_setup<2><<<gg, 256, 0, s>>>(C.m, C.S64, C.lam64);
+    else k_fdm_setup<3><<<gg, 256, 0, s>>>(C.m, C.S64, C.lam64);
+    DCG_LAUNCH_CHECK();
+    if (fp32) {
+      DCG_CUDA(cudaMalloc(&C.S32, sizeof(float) * C.m * C.m));
+      DCG_CUDA(cudaMalloc(&C.lam32, sizeof(float) * nn));
+      k_to_t<float><<<grid_for(C.m * C.m, 256), 256, 0, s>>>(C.S64, C.S32, (long long)C.m * C.m);
+      k_to_t<float><<<grid_for(nn, 256), 256, 0, s>>>(C.lam64, C.lam32, nn);
+      DCG_LAUNCH_CHECK();
+    }
+  }
+  // RAS kernel shared memory opt-in
+  size_t smem_max = 0;
+  for (auto& L : p->levels) smem_max = std::max(smem_max, fp32 ? ras_smem_bytes<float>(L.npmax) : ras_smem_bytes<double>(L.npmax));
+  if (smem_max > 48 * 1024) {
+    if (fp32) {
+      DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+      DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    } else {
+      DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+      DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    }
+  }
+  DCG_CUDA(cudaStreamSynchronize(s));
+  if (!exact_mode(p)) DCG_TRY(build_wcycle_graph(p));
+  return DCG_OK;
+}
+
+int mg_inner_apply(dcg_problem* p, const double* z, double* y, cudaStream_t s) {
+  if (p->levels.empty()) return DCG_ERR_STATE;
+  Level& L = p->levels.back();
+  const int g = grid_for(L.nn, 256, 8192);
+  if (p->dim == 2) k_apply<double, 2><<<g, 256, 0, s>>>(L.st64, z, y, L.m, L.nn);
+  else k_apply<double, 3><<<g, 256, 0, s>>>(L.st64, z, y, L.m, L.nn);
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
+
+namespace {
+
+template <typename T>
+int inner_residual(dcg_problem* p, const double* g, const double* z, cudaStream_t s) {
+  Level& L = p->levels.back();
+  const int grid = grid_for(L.nn, 256, 4096);
+  Reduce red = make_reduce(p, S_TMP0);  // S_TMP0 <- ||r||^2, S_TMP1 <- ||g||^2
+  if (p->dim == 2)
+    k_inner_residual<T, 2><<<grid, 256, 0, s>>>(L.st64, g, z, (T*)L.f, (T*)L.z, nullptr, L.m, L.nn, red);
+  else
+    k_inner_residual<T, 3><<<grid, 256, 0, s>>>(L.st64, g, z, (T*)L.f, (T*)L.z, nullptr, L.m, L.nn, red);
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
+
+template <typename T>
+int accumulate(dcg_problem* p, double* z, cudaStream_t s) {
+  Level& L = p->levels.back();
+  k_accumulate<T><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(z, (const T*)L.z, L.nn);
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
+
+// exact inner solve: z = Z_J^-1 g by fast diagonalisation (FP64)
+int exact_solve(dcg_problem* p, const double* g, double* z, cudaStream_t s) {
+  Level& L = p->levels.back();
+  DCG_CUDA(cudaMemcpyAsync(L.f, g, sizeof(double) * L.nn, cudaMemcpyDeviceToDevice, s));
+  int st = p->dim == 2 ? coarse_solve_t<double, 2>(p, (const double*)L.f, (double*)L.z, s)
+                       : coarse_solve_t<double, 3>(p, (const double*)L.f, (double*)L.z, s);
+  if (st != DCG_OK) return st;
+  DCG_CUDA(cudaMemcpyAsync(z, L.z, sizeof(double) * L.nn, cudaMemcpyDeviceToDevice, s));
+  return DCG_OK;
+}
+
+}  // namespace
+
+int mg_cycles(dcg_problem* p, const double* g, double* z, int ncycles, cudaStream_t s) {
+  if (p->levels.empty()) return DCG_ERR_STATE;
+  if (exact_mode(p)) return exact_solve(p, g, z, s);
+  const bool fp32 = g_state[p].fp32;
+  for (int c = 0; c < ncycles; ++c) {
+    DCG_TRY(fp32 ? inner_residual<float>(p, g, z, s) : inner_residual<double>(p, g, z, s));
+    DCG_TRY(run_wcycle(p, s));
+    DCG_TRY(fp32 ? accumulate<float>(p, z, s) : accumulate<double>(p, z, s));
+  }
+  return DCG_OK;
+}
+
+int mg_solve(dcg_problem* p, const double* g, double* z, double tol, int nmax, int* ncyc, cudaStream_t s) {
+  if (p->levels.empty()) return DCG_ERR_STATE;
+  *ncyc = 0;
+  if (exact_mode(p)) return exact_solve(p, g, z, s);
+  const bool fp32 = g_state[p].fp32;
+  int n = 0;
+  for (;;) {
+    DCG_TRY(fp32 ? inner_residual<float>(p, g, z, s) : inner_residual<double>(p, g, z, s));
+    DCG_TRY(read_scalars(p, s));
+    const double rn = std::sqrt(p->scal_host[S_TMP0]);
+    const double gn = std::sqrt(p->scal_host[S_TMP1]);
+    if (!(gn > 0.0)) break;
+    if (!(rn / gn > tol) || n >= nmax) break;
+    DCG_TRY(run_wcycle(p, s));
+    DCG_TRY(fp32 ? accumulate<float>(p, z, s) : accumulate<double>(p, z, s));
+    ++n;
+  }
+  *ncyc = n;
+  return DCG_OK;
+}
+
+int mg_ras_step_hook(dcg_problem* p, int level, const double* f, double* z, cudaStream_t s) {
+  if (level < 2 || level > (int)p->levels.size()) return DCG_ERR_INVALID_ARG;
+  Level& L = p->levels[level - 1];
+  const bool fp32 = g_state[p].fp32;
+  const int g = grid_for(L.nn, 256, 8192);
+  if (fp32) {
+    k_to_t<float><<<g, 256, 0, s>>>(f, (float*)L.f, L.nn);
+    k_to_t<float><<<g, 256, 0, s>>>(z, (float*)L.z, L.nn);
+    DCG_TRY(p->dim == 2 ? (ras_step_t<float, 2>(p, L, s)) : (ras_step_t<float, 3>(p, L, s)));
+    k_from_t<float><<<g, 256, 0, s>>>((const float*)L.z, z, L.nn);
+  } else {
+    DCG_CUDA(cudaMemcpyAsync(L.f, f, sizeof(double) * L.nn, cudaMemcpyDeviceToDevice, s));
+    DCG_CUDA(cudaMemcpyAsync(L.z, z, sizeof(double) * L.nn, cudaMemcpyDeviceToDevice, s));
+    DCG_TRY(p->dim == 2 ? (ras_step_t<double, 2>(p, L, s)) : (ras_step_t<double, 3>(p, L, s)));
+    DCG_CUDA(cudaMemcpyAsync(z, L.z, sizeof(double) * L.nn, cudaMemcpyDeviceToDevice, s));
+  }
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
+
+int mg_coarse_hook(dcg_problem* p, const double* f, double* z, cudaStream_t s) {
+  if (p->levels.empty()) return DCG_ERR_STATE;
+  Level& L = p->levels[0];
+  const bool fp32 = g_state[p].fp32;
+  const int g = grid_for(L.nn, 256, 8192);
+  if (fp32) {
+    k_to_t<float><<<g, 256, 0, s>>>(f, (float*)L.f, L.nn);
+    DCG_TRY(p->dim == 2 ? (coarse_solve_t<float, 2>(p, (const float*)L.f, (float*)L.z, s))
+                        : (coarse_solve_t<float, 3>(p, (const float*)L.f, (float*)L.z, s)));
+    k_from_t<float><<<g, 256, 0, s>>>((const float*)L.z, z, L.nn);
+  } else {
+    DCG_CUDA(cudaMemcpyAsync(L.f, f, sizeof(double) * L.nn, cudaMemcpyDeviceToDevice, s));
+    DCG_TRY(p->dim == 2 ? (coarse_solve_t<double, 2>(p, (const double*)L.f, (double*)L.z, s))
+                        : (coarse_solve_t<double, 3>(p, (const double*)L.f, (double*)L.z, s)));
+    DCG_CUDA(cudaMemcpyAsync(z, L.z, sizeof(double) * L.nn, cudaMemcpyDeviceToDevice, s));
+  }
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
+
+}  // namespace dcg

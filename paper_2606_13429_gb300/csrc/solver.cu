@@ -1,0 +1,344 @@
+// Outer solvers on the device, FP64: plain CG, and the flexible deflated CG
+// of Algorithm 2 with the FCG recurrences of Algorithm 1.
+//
+//   pi(z)   = V Multigrid(V^T z, tau_c)                          (Algorithm 2)
+//   M_D(d)  = A (d - pi(A d))                                    (Algorithm 2)
+//   f_D     = f - A pi(f)   (the right-hand side of Eq. defl_sys, (I - pi_A)^T f)
+//   x_hat   = FCG(f_D, x0, M_D)                                  (Algorithm 1)
+//   x       = x_hat - pi(A x_hat) + pi(f)                        (Eq. x_defl)
+//
+// Outer stop ||r_i|| <= tol ||f|| on the recursive deflated residual
+// (Section 4.1). Inner tolerance relative to ||V^T A d||: fixed
+// tau_c = c tol (Eq. fixed_tol with c = c_F) or adaptive
+// tau_c = c tol ||f|| / ||r_i|| (Eq. tol, c = c_A). pi(f) appears twice in
+// Algorithm 2 with the same arguments and is computed once.
+// After reconstruction the true residual ||f - A x|| / ||f|| is computed in
+// FP64; above tol, the same solver runs on A e = f - A x (same absolute
+// threshold) and x += e, at most max_restarts times.
+//
+// Per outer iteration (kernels, all FP64 except the W-cycle):
+//   g = V^T A d            (SpMV reading only the diagonal-component rows)
+//   zh = MG(g)             (Algorithm 3; one host read per W-cycle)
+//   q = A (d - V zh), d.q  (SpMV with the embed in its operand gather)
+//   x += a d, r -= a q, r.r, r.q     (a from device scalars)
+//   d = r -+ b d, d.r       (b from device scalars)
+// and one host read of ||r|| for the stopping test.
+#include "common.cuh"
+
+#include <chrono>
+#include <cmath>
+
+namespace dcg {
+namespace {
+
+enum Rule { R_CG = 0, R_FCG1 = 1, R_FR = 2, R_FCGINF = 3 };
+
+// x += a d; r -= a q; reduces (r.r, r.q) into (S_RRN, S_RQ);
+// a = (FCG ? d.r : r.r) / d.q, zero when d.q <= 0 (breakdown: the host stops).
+__global__ void k_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ d,
+                         const double* __restrict__ q, long long n, const double* __restrict__ sc, int use_dr,
+                         Reduce red) {
+  const double dq = sc[S_DQ];
+  const double num = use_dr ? sc[S_DR] : sc[S_RR];
+  const double a = (dq > 0.0) ? num / dq : 0.0;
+  double part[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double di = d[i], qi = q[i];
+    x[i] = fma(a, di, x[i]);
+    const double ri = fma(-a, qi, r[i]);
+    r[i] = ri;
+    part[0] = fma(ri, ri, part[0]);
+    part[1] = fma(ri, qi, part[1]);
+  }
+  grid_reduce<2>(part, red);
+  if (blockIdx.x == 0 && threadIdx.x == 0) ((double*)sc)[S_ALPHA] = a;
+}
+
+// FR:   d = r + (rr_new / rr) d
+// FCG1: d = r - (rq / dq) d
+// then d.r -> S_DR and S_RR <- rr_new
+__global__ void k_direction(double* __restrict__ d, const double* __restrict__ r, long long n, double* __restrict__ sc,
+                            int fcg, Reduce red) {
+  const double rrn = sc[S_RRN];  // r.r of the new residual (written by k_update)
+  const double beta = fcg ? -(sc[S_RQ] / sc[S_DQ]) : rrn / sc[S_RR];
+  double part[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double ri = r[i];
+    const double di = fma(beta, d[i], ri);
+    d[i] = di;
+    part[0] = fma(di, ri, part[0]);
+  }
+  grid_reduce<1>(part, red);  // -> S_DR
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc[S_BETA] = beta;
+}
+
+// after k_direction has read both: S_RR <- S_RRN
+__global__ void k_roll(double* sc) { sc[S_RR] = sc[S_RRN]; }
+
+// FCG(inf): d = r - sum_k (c_k / dq_k) d_k
+__global__ void k_orth_direction(double* __restrict__ d, const double* __restrict__ r, const double* __restrict__ dirs,
+                                 const double* __restrict__ coef, const double* __restrict__ dqs, int K, long long n,
+                                 Reduce red) {
+  double part[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double ri = r[i];
+    double di = ri;
+    for (int k = 0; k < K; ++k) di = fma(-(coef[k] / dqs[k]), dirs[(size_t)k * n + i], di);
+    d[i] = di;
+    part[0] = fma(di, ri, part[0]);
+  }
+  grid_reduce<1>(part, red);
+}
+
+// x = xh - V (z1 - zf) (Eq. x_defl with pi(A xh) = V z1, pi(f) = V zf)
+template <int D>
+__global__ void k_reconstruct(const double* __restrict__ xh, const double* __restrict__ z1, const double* __restrict__ zf,
+                              double* __restrict__ x, long long nn, double isd) {
+  constexpr int B = D * D;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn * B; t += (long long)gridDim.x * blockDim.x) {
+    const long long a = t / B;
+    const int c = (int)(t % B);
+    double v = xh[t];
+    if (c % (D + 1) == 0) v = v - isd * z1[a] + isd * zf[a];
+    x[t] = v;
+  }
+}
+
+__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
+__global__ void k_sub(double* __restrict__ y, const double* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] -= x[i];
+}
+
+__global__ void k_set_slot(double* sc, int dst, int src) { sc[dst] = sc[src]; }
+
+struct Ctx {
+  dcg_problem* p;
+  cudaStream_t s;
+  dcg_stats* st;
+  double tol, eps, fnorm;
+  int max_it;
+  int rule;
+};
+
+int grid_n(long long n) { return grid_for(n, kRedThreads, 1184); }
+
+double inner_tol(const Ctx& c, double rnorm) {
+  const dcg_options& o = c.p->opts;
+  if (o.inner_rule == DCG_INNER_ADAPTIVE) return o.c * c.eps / rnorm;
+  return o.c * c.tol;
+}
+
+// zh = MG(V^T A x) into `z` (zeroed first), counting cycles
+int pi_of_Ax(Ctx& c, const double* x, double* z, double tc, bool in_iter) {
+  dcg_problem* p = c.p;
+  SolverBuffers& b = p->sb;
+  DCG_TRY(spmv_vt(p, x, b.g, S_GG, c.s));
+  DCG_TRY(vec_zero(z, p->n_nodes, c.s));
+  int n = 0;
+  DCG_TRY(mg_solve(p, b.g, z, tc, p->opts.inner_nmax, &n, c.s));
+  c.st->total_mg_cycles += n;
+  if (in_iter) c.st->iter_mg_cycles += n;
+  return DCG_OK;
+}
+
+// one FDCG pass: solve A x = f, x0 from x (if use_x0), result into x
+int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged) {
+  dcg_problem* p = c.p;
+  SolverBuffers& b = p->sb;
+  cudaStream_t s = c.s;
+  const long long N = p->N;
+  const double tc0 = p->opts.c * c.tol;
+  *converged = false;
+  // pi(f): zf = MG(V^T f)
+  DCG_TRY(vec_extract(p, f, b.g, S_GG, s));
+  DCG_TRY(vec_zero(b.zf, p->n_nodes, s));
+  {
+    int n = 0;
+    DCG_TRY(mg_solve(p, b.g, b.zf, tc0, p->opts.inner_nmax, &n, s));
+    c.st->total_mg_cycles += n;
+  }
+  // r = f_D = f - A V zf
+  DCG_TRY(spmv_f_minus_avz(p, f, b.zf, b.r, S_RR, s));
+  if (use_x0) {
+    DCG_TRY(vec_copy(b.xh, x, N, s));
+    // r -= M_D x0 = A (x0 - pi(A x0))
+    DCG_TRY(pi_of_Ax(c, b.xh, b.zh, tc0, false));
+    DCG_TRY(spmv_defl(p, b.xh, b.zh, b.q, S_TMP0, s));
+    k_sub<<<grid_n(N), kRedThreads, 0, s>>>(b.r, b.q, N);
+    DCG_LAUNCH_CHECK();
+    DCG_TRY(vec_dot(p, b.r, b.r, N, S_RR, s));
+  } else {
+    DCG_TRY(vec_zero(b.xh, N, s));
+  }
+  DCG_TRY(vec_copy(b.d, b.r, N, s));
+  k_set_slot<<<1, 1, 0, s>>>(p->scal, S_DR, S_RR);
+  DCG_LAUNCH_CHECK();
+  DCG_TRY(read_scalars(p, s));
+  double rr = p->scal_host[S_RR];
+  if (std::sqrt(rr) <= c.eps) *converged = true;
+  const bool fcginf = c.rule == R_FCGINF;
+  int ndir = 0;
+  while (!*converged && c.st->outer_its < c.max_it) {
+    const double rnorm = std::sqrt(rr);
+    const double tc = inner_tol(c, rnorm);
+    // q = M_D d
+    DCG_TRY(pi_of_Ax(c, b.d, b.zh, tc, true));
+    DCG_TRY(spmv_defl(p, b.d, b.zh, b.q, S_DQ, s));
+    if (fcginf) {
+      // store d_k, q_k before the update (ring buffer of ndir_cap)
+      const int slot = ndir % b.ndir_cap;
+      DCG_TRY(vec_copy(b.dirs + (size_t)slot * N, b.d, N, s));
+      DCG_TRY(vec_copy(b.qdirs + (size_t)slot * N, b.q, N, s));
+      DCG_CUDA(cudaMemcpyAsync(b.coef + b.ndir_cap + slot, p->scal + S_DQ, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      ++ndir;
+    }
+    k_update<<<grid_n(N), kRedThreads, 0, s>>>(b.xh, b.r, b.d, b.q, N, p->scal, c.rule != R_FR,
+                                               make_reduce(p, S_RRN));
+    DCG_LAUNCH_CHECK();
+    c.st->outer_its++;
+    DCG_TRY(read_scalars(p, s));
+    const double dq = p->scal_host[S_DQ];
+    const double rrn = p->scal_host[S_RRN];
+    if (!(dq > 0.0) || !std::isfinite(dq) || !std::isfinite(rrn)) {
+      c.st->status = DCG_ERR_BREAKDOWN;
+      break;
+    }
+    if (std::sqrt(rrn) <= c.eps) {
+      *converged = true;
+      break;
+    }
+    if (fcginf) {
+      const int K = ndir < b.ndir_cap ? ndir : b.ndir_cap;
+      for (int k = 0; k < K; ++k) {
+        const double* qk = b.qdirs + (size_t)k * N;
+        // c_k = r . q_k
+        DCG_TRY(vec_dot(p, b.r, qk, N, S_TMP0, s));
+        DCG_CUDA(cudaMemcpyAsync(b.coef + k, p->scal + S_TMP0, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      }
+      k_orth_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, b.dirs, b.coef, b.coef + b.ndir_cap, K, N,
+                                                          make_reduce(p, S_DR));
+      DCG_LAUNCH_CHECK();
+    } else {
+      k_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, N, p->scal, c.rule == R_FCG1, make_reduce(p, S_DR));
+      DCG_LAUNCH_CHECK();
+    }
+    k_roll<<<1, 1, 0, s>>>(p->scal);
+    DCG_LAUNCH_CHECK();
+    rr = rrn;
+  }
+  // reconstruction x = xh - pi(A xh) + pi(f)
+  DCG_TRY(pi_of_Ax(c, b.xh, b.zh, tc0, false));
+  const int g = grid_n(N);
+  const double isd = 1.0 / std::sqrt((double)p->dim);
+  if (p->dim == 2) k_reconstruct<2><<<g, kRedThreads, 0, s>>>(b.xh, b.zh, b.zf, x, p->n_nodes, isd);
+  else k_reconstruct<3><<<g, kRedThreads, 0, s>>>(b.xh, b.zh, b.zf, x, p->n_nodes, isd);
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
+
+int plain_cg(Ctx& c, const double* f, double* x) {
+  dcg_problem* p = c.p;
+  SolverBuffers& b = p->sb;
+  cudaStream_t s = c.s;
+  const long long N = p->N;
+  DCG_TRY(spmv_residual(p, f, x, b.r, S_RR, s));
+  DCG_TRY(vec_copy(b.d, b.r, N, s));
+  DCG_TRY(read_scalars(p, s));
+  double rr = p->scal_host[S_RR];
+  bool conv = std::sqrt(rr) <= c.eps;
+  while (!conv && c.st->outer_its < c.max_it) {
+    DCG_TRY(spmv_dot(p, b.d, b.q, b.d, S_DQ, s));
+    k_update<<<grid_n(N), kRedThreads, 0, s>>>(x, b.r, b.d, b.q, N, p->scal, 0, make_reduce(p, S_RRN));
+    DCG_LAUNCH_CHECK();
+    c.st->outer_its++;
+    bool check = (c.st->outer_its % std::max(1, p->opts.check_every)) == 0;
+    if (check) {
+      DCG_TRY(read_scalars(p, s));
+      const double dq = p->scal_host[S_DQ];
+      const double rrn = p->scal_host[S_RRN];
+      if (!(dq > 0.0) || !std::isfinite(rrn)) {
+        c.st->status = DCG_ERR_BREAKDOWN;
+        break;
+      }
+      if (std::sqrt(rrn) <= c.eps) {
+        conv = true;
+        break;
+      }
+    }
+    k_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, N, p->scal, 0, make_reduce(p, S_DR));
+    DCG_LAUNCH_CHECK();
+    k_roll<<<1, 1, 0, s>>>(p->scal);
+    DCG_LAUNCH_CHECK();
+  }
+  return DCG_OK;
+}
+
+}  // namespace
+
+int read_scalars(dcg_problem* p, cudaStream_t s) {
+  DCG_CUDA(cudaMemcpyAsync(p->scal_host, p->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
+  DCG_CUDA(cudaStreamSynchronize(s));
+  return DCG_OK;
+}
+
+int solve_device(dcg_problem* p, const double* f, double* x, double tol, int max_it, dcg_stats* st,
+                 cudaStream_t s) {
+  auto t0 = std::chrono::steady_clock::now();
+  *st = dcg_stats{};
+  st->status = DCG_OK;
+  Ctx c{p, s, st, tol, 0.0, 0.0, max_it, R_CG};
+  const dcg_options& o = p->opts;
+  if (o.deflate) {
+    c.rule = o.recurrence == DCG_FR ? R_FR : (o.recurrence == DCG_FCG_INF ? R_FCGINF : R_FCG1);
+  }
+  const long long N = p->N;
+  SolverBuffers& b = p->sb;
+  DCG_TRY(vec_dot(p, f, f, N, S_FF, s));
+  DCG_TRY(vec_dot(p, x, x, N, S_TMP1, s));
+  DCG_TRY(read_scalars(p, s));
+  c.fnorm = std::sqrt(p->scal_host[S_FF]);
+  const bool x0_nonzero = p->scal_host[S_TMP1] != 0.0;
+  if (!(c.fnorm > 0.0)) {
+    DCG_TRY(vec_zero(x, N, s));
+    DCG_CUDA(cudaStreamSynchronize(s));
+    st->true_relres = 0.0;
+    return DCG_OK;
+  }
+  c.eps = tol * c.fnorm;
+  if (!o.deflate) {
+    DCG_TRY(plain_cg(c, f, x));
+  } else {
+    if (c.rule == R_FCGINF && !b.dirs) return DCG_ERR_STATE;
+    bool conv = false;
+    DCG_TRY(fdcg_pass(c, f, x, x0_nonzero, &conv));
+  }
+  // true residual
+  DCG_TRY(spmv_residual(p, f, x, b.u, S_TMP0, s));
+  DCG_TRY(read_scalars(p, s));
+  st->true_relres = std::sqrt(p->scal_host[S_TMP0]) / c.fnorm;
+  if (o.deflate) {
+    while (st->true_relres > tol && st->restarts < o.max_restarts && st->status == DCG_OK &&
+           st->outer_its < max_it) {
+      st->restarts++;
+      bool conv = false;
+      DCG_TRY(fdcg_pass(c, b.u, b.e, false, &conv));
+      k_axpy<<<grid_n(N), kRedThreads, 0, s>>>(x, b.e, N);
+      DCG_LAUNCH_CHECK();
+      DCG_TRY(spmv_residual(p, f, x, b.u, S_TMP0, s));
+      DCG_TRY(read_scalars(p, s));
+      st->true_relres = std::sqrt(p->scal_host[S_TMP0]) / c.fnorm;
+    }
+  }
+  DCG_CUDA(cudaStreamSynchronize(s));
+  if (st->status == DCG_OK && !(st->true_relres <= tol)) st->status = DCG_ERR_NOT_CONVERGED;
+  st->avg_inner = st->outer_its ? (double)st->iter_mg_cycles / st->outer_its : 0.0;
+  st->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return st->status;
+}
+
+}  // namespace dcg

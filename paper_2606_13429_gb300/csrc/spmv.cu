@@ -1,0 +1,218 @@
+// FP64 BSR SpMV for the pseudo-stress operator, with the deflation
+// embed/extract and the CG dot products fused into its prologue/epilogue.
+//
+// Mapping: a CTA owns 32 consecutive block rows; warp w computes scalar row
+// R(w) of each of them (lane = block row). Every warp therefore executes one
+// row pattern, so the structural zeros of the block (Section 3.1: the block is
+// (1/dt) mt D_d + kron(I_d, G), 10 of 16 entries in 2D, 33 of 81 in 3D) are
+// skipped without divergence. A lane reads the b contiguous doubles of its
+// block row chunk (one 32-byte sector in 2D) and the b doubles of x at the
+// column block.
+//
+// Variants (x operand / output):
+//   x            : y = A x
+//   x - V zh     : q = A (d - V zh)          (M_D of Algorithm 2, second product)
+//   V zh         : y = A V zh                 (A pi(f) for f_D)
+//   out = y / f - y / V^T y (only the d diagonal-component rows are computed:
+//   g = V^T A x reads half (2D) or a third (3D) of the matrix).
+#include "common.cuh"
+
+namespace dcg {
+namespace {
+
+enum XMode { XM_X = 0, XM_X_MINUS_VZ = 1, XM_VZ = 2 };
+enum OMode { OM_Y = 0, OM_FMY = 1, OM_VT = 2 };
+
+struct SpmvArgs {
+  const int* row_ptr;
+  const int* col_idx;
+  const double* vals;
+  long long n_nodes;
+  const double* x;
+  const double* zh;
+  const double* f;
+  double* y;
+  const double* dvec;  // dot(dvec, y) for OM_Y
+  double isd;          // 1/sqrt(d)
+  Reduce red;
+};
+
+template <int D, int XM>
+__device__ __forceinline__ double xval(const SpmvArgs& A, long long c, int col) {
+  constexpr int B = D * D;
+  const bool diag = (col % (D + 1)) == 0;  // positions l*D+l
+  if (XM == XM_X) return __ldg(A.x + c * B + col);
+  if (XM == XM_VZ) return diag ? __dmul_rn(A.isd, __ldg(A.zh + c)) : 0.0;
+  // XM_X_MINUS_VZ
+  double v = __ldg(A.x + c * B + col);
+  return diag ? __dsub_rn(v, __dmul_rn(A.isd, __ldg(A.zh + c))) : v;
+}
+
+// Sum over the block row of row R restricted to structural nonzeros.
+template <int D, int R, int XM>
+__device__ __forceinline__ double row_sum(const SpmvArgs& A, int j0, int j1) {
+  constexpr int B = D * D;
+  constexpr int k = R / D, i = R % D;
+  double acc = 0.0;
+  for (int j = j0; j < j1; ++j) {
+    const long long c = __ldg(A.col_idx + j);
+    const double* v = A.vals + (long long)j * (B * B) + R * B;
+    if (k == i) {
+#pragma unroll
+      for (int l = 0; l < D; ++l) acc = fma(__ldg(v + l * D + l), xval<D, XM>(A, c, l * D + l), acc);
+#pragma unroll
+      for (int q = 0; q < D; ++q)
+        if (q != k) acc = fma(__ldg(v + k * D + q), xval<D, XM>(A, c, k * D + q), acc);
+    } else {
+#pragma unroll
+      for (int q = 0; q < D; ++q) acc = fma(__ldg(v + k * D + q), xval<D, XM>(A, c, k * D + q), acc);
+    }
+  }
+  return acc;
+}
+
+template <int D, int XM>
+__device__ __forceinline__ double row_dispatch(const SpmvArgs& A, int R, int j0, int j1) {
+  switch (R) {
+    case 0: return row_sum<D, 0, XM>(A, j0, j1);
+    case 1: return row_sum<D, 1, XM>(A, j0, j1);
+    case 2: return row_sum<D, 2, XM>(A, j0, j1);
+    case 3: return row_sum<D, 3, XM>(A, j0, j1);
+    default: break;
+  }
+  if constexpr (D == 3) {
+    switch (R) {
+      case 4: return row_sum<D, 4, XM>(A, j0, j1);
+      case 5: return row_sum<D, 5, XM>(A, j0, j1);
+      case 6: return row_sum<D, 6, XM>(A, j0, j1);
+      case 7: return row_sum<D, 7, XM>(A, j0, j1);
+      case 8: return row_sum<D, 8, XM>(A, j0, j1);
+      default: break;
+    }
+  }
+  return 0.0;
+}
+
+template <int D, int XM, int OM, bool DOT>
+__global__ void k_spmv(SpmvArgs A) {
+  constexpr int B = D * D;
+  constexpr int NW = (OM == OM_VT) ? D : B;
+  __shared__ double s_rows[NW][32];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int R = (OM == OM_VT) ? w * D + w : w;
+  double part[1] = {0.0};
+  for (long long base = (long long)blockIdx.x * 32; base < A.n_nodes; base += (long long)gridDim.x * 32) {
+    const long long a = base + lane;
+    double acc = 0.0;
+    if (a < A.n_nodes) {
+      const int j0 = __ldg(A.row_ptr + a), j1 = __ldg(A.row_ptr + a + 1);
+      acc = row_dispatch<D, XM>(A, R, j0, j1);
+    }
+    if (OM == OM_VT) {
+      s_rows[w][lane] = acc;
+      __syncthreads();
+      if (w == 0 && a < A.n_nodes) {
+        double s = s_rows[0][lane];
+#pragma unroll
+        for (int l = 1; l < D; ++l) s += s_rows[l][lane];
+        const double g = s * A.isd;
+        A.y[a] = g;
+        if (DOT) part[0] = fma(g, g, part[0]);
+      }
+      __syncthreads();
+    } else if (a < A.n_nodes) {
+      const long long row = a * B + R;
+      double out = acc;
+      if (OM == OM_FMY) out = __dsub_rn(A.f[row], acc);
+      A.y[row] = out;
+      if (DOT) {
+        if (OM == OM_FMY) part[0] = fma(out, out, part[0]);
+        else part[0] = fma(A.dvec[row], out, part[0]);
+      }
+    }
+  }
+  if (DOT) grid_reduce<1>(part, A.red);
+}
+
+template <int XM, int OM, bool DOT>
+int launch(dcg_problem* p, SpmvArgs a, cudaStream_t s) {
+  if (p->matrix_free) {
+    set_error_msg("BSR product requested on a matrix-free problem");
+    return DCG_ERR_UNSUPPORTED;
+  }
+  a.row_ptr = p->row_ptr;
+  a.col_idx = p->col_idx;
+  a.vals = p->vals;
+  a.n_nodes = p->n_nodes;
+  a.isd = 1.0 / sqrt((double)p->dim);
+  const int grid = grid_for(p->n_nodes, 32);
+  if (p->dim == 2) {
+    const int threads = 32 * (OM == OM_VT ? 2 : 4);
+    k_spmv<2, XM, OM, DOT><<<grid, threads, 0, s>>>(a);
+  } else {
+    const int threads = 32 * (OM == OM_VT ? 3 : 9);
+    k_spmv<3, XM, OM, DOT><<<grid, threads, 0, s>>>(a);
+  }
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
+
+}  // namespace
+
+int spmv_plain(dcg_problem* p, const double* x, double* y, cudaStream_t s) {
+  SpmvArgs a{};
+  a.x = x;
+  a.y = y;
+  return launch<XM_X, OM_Y, false>(p, a, s);
+}
+
+int spmv_dot(dcg_problem* p, const double* x, double* y, const double* dv, int slot, cudaStream_t s) {
+  SpmvArgs a{};
+  a.x = x;
+  a.y = y;
+  a.dvec = dv;
+  a.red = make_reduce(p, slot);
+  if (!dv) return launch<XM_X, OM_Y, false>(p, a, s);
+  return launch<XM_X, OM_Y, true>(p, a, s);
+}
+
+int spmv_residual(dcg_problem* p, const double* f, const double* x, double* y, int slot, cudaStream_t s) {
+  SpmvArgs a{};
+  a.x = x;
+  a.f = f;
+  a.y = y;
+  a.red = make_reduce(p, slot);
+  return launch<XM_X, OM_FMY, true>(p, a, s);
+}
+
+int spmv_vt(dcg_problem* p, const double* x, double* g, int slot, cudaStream_t s) {
+  SpmvArgs a{};
+  a.x = x;
+  a.y = g;
+  a.red = make_reduce(p, slot);
+  return launch<XM_X, OM_VT, true>(p, a, s);
+}
+
+int spmv_defl(dcg_problem* p, const double* x, const double* zh, double* q, int slot, cudaStream_t s) {
+  SpmvArgs a{};
+  a.x = x;
+  a.zh = zh;
+  a.y = q;
+  a.dvec = x;
+  a.red = make_reduce(p, slot);
+  if (!x) return launch<XM_VZ, OM_Y, false>(p, a, s);
+  if (!zh) return launch<XM_X, OM_Y, true>(p, a, s);
+  return launch<XM_X_MINUS_VZ, OM_Y, true>(p, a, s);
+}
+
+int spmv_f_minus_avz(dcg_problem* p, const double* f, const double* zh, double* y, int slot, cudaStream_t s) {
+  SpmvArgs a{};
+  a.zh = zh;
+  a.f = f;
+  a.y = y;
+  a.red = make_reduce(p, slot);
+  return launch<XM_VZ, OM_FMY, true>(p, a, s);
+}
+
+}  // namespace dcg

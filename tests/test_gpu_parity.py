@@ -1,0 +1,349 @@
+"""GPU parity: every kernel of the hot path, called through the C ABI, against
+the FP64 oracle on the same seeded inputs.
+
+Bars: indices bit-exact; FP64 assembly values to 1e-14 relative; FP64 SpMV,
+embed/extract and stencil products to 1e-12; FP64 smoother, coarse solve and
+W-cycles to 1e-10; solves at true relative residual 1e-8 to 1e-7 relative
+error with outer iteration counts within +-2. Mixed precision (FP32
+W-cycle) is held to its own bars (FP32 rounding, ~1e-5) and the same
+true-residual target.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fem, mg, solvers
+from paper_2606_13429_gb300 import dcg, inputs
+
+pytestmark = pytest.mark.gpu
+
+SMALL = [(2, 32), (2, 21), (3, 8), (3, 11)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2606_13429_gb300 import build
+    build.build()
+    dcg.load()
+    torch.cuda.set_device(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def mg_opts(patch=4, overlap=1, m1=2, m2=2, max_levels=4, weights="multiplicity"):
+    return mg.MGOptions(patch=patch, overlap=overlap, m1=m1, m2=m2, max_levels=max_levels, ras_weights=weights)
+
+
+def gpu_opts(o: mg.MGOptions, **kw):
+    return dcg.options(patch=o.patch, overlap=o.overlap, m1=o.m1, m2=o.m2, max_levels=o.max_levels,
+                       ras_weights=dcg.DCG_RAS_RESTRICTED if o.ras_weights == "restricted" else dcg.DCG_RAS_MULTIPLICITY,
+                       **kw)
+
+
+# --------------------------------------------------------------------------- assembly
+
+
+@pytest.mark.parametrize("d,n", SMALL + [(2, 1024), (3, 48)])
+def test_pattern_bit_exact(d, n):
+    prob = dcg.dcg_assemble(d, n, 1e-3)
+    rp, ci = dcg.dcg_export_pattern(prob)
+    rp_o, ci_o = fem.bsr_pattern(fem.Mesh(d, n))
+    assert np.array_equal(rp, rp_o) and np.array_equal(ci, ci_o)
+
+
+@pytest.mark.parametrize("d,n", [(2, 32), (2, 7), (3, 8), (3, 5)])
+@pytest.mark.parametrize("dt", [1e-1, 1e-6])
+@pytest.mark.parametrize("per_elem", [False, True])
+def test_values(d, n, dt, per_elem):
+    nu_e = inputs.nu_elements(5, n ** d) if per_elem else None
+    prob = dcg.dcg_assemble(d, n, dt, nu=1.0, nu_elem=nu_e)
+    v = dcg.dcg_export_values(prob)
+    asm = fem.assemble(d, n, dt, nu_elem=nu_e)
+    scale = np.abs(asm.values).max()
+    assert np.abs(v - asm.values).max() <= 1e-14 * scale
+    # the assembly uses round-to-nearest operations in the oracle's order
+    assert np.mean(v == asm.values) > 0.999
+
+
+# --------------------------------------------------------------------------- SpMV and deflation
+
+
+@pytest.mark.parametrize("d,n", SMALL)
+@pytest.mark.parametrize("dt", [1e-1, 1e-4])
+def test_spmv(d, n, dt):
+    asm = fem.assemble(d, n, dt)
+    prob = dcg.dcg_assemble(d, n, dt)
+    x = inputs.rhs(7, asm.mesh.n_unknowns)
+    y = torch.empty(prob.N, dtype=torch.float64, device="cuda")
+    dcg.dcg_spmv(prob, dev(x), y)
+    assert relerr(host(y), asm.matrix() @ x) <= 1e-12
+
+
+@pytest.mark.parametrize("d,n", [(2, 1024), (3, 128)])
+def test_spmv_full_size_sampled_rows(d, n):
+    """The bench's operators: sampled block rows against the oracle's
+    one-node-at-a-time product (first, last, boundary and random nodes)."""
+    dt = 1e-4
+    prob = dcg.dcg_assemble(d, n, dt)
+    mesh = fem.Mesh(d, n)
+    x = inputs.rhs(11, mesh.n_unknowns)
+    y = torch.empty(prob.N, dtype=torch.float64, device="cuda")
+    dcg.dcg_spmv(prob, dev(x), y)
+    yh = host(y).reshape(mesh.n_nodes, mesh.b)
+    rng = np.random.default_rng(0)
+    nodes = np.unique(np.concatenate([[0, 1, mesh.m - 1, mesh.m, mesh.n_nodes // 2, mesh.n_nodes - 1],
+                                      rng.integers(0, mesh.n_nodes, 40)]))
+    want = fem.rows_of_Ax(mesh, dt, x, nodes)
+    assert relerr(yh[nodes], want) <= 1e-12
+    prob.close()
+
+
+@pytest.mark.parametrize("d,n", [(2, 21), (3, 8)])
+def test_embed_extract(d, n):
+    prob = dcg.dcg_assemble(d, n, 1e-3)
+    mesh = fem.Mesh(d, n)
+    y = inputs.rhs(3, mesh.n_unknowns)
+    q = torch.empty(prob.n_nodes, dtype=torch.float64, device="cuda")
+    dcg.dcg_extract(prob, dev(y), q)
+    assert relerr(host(q), fem.extract(mesh, y)) <= 1e-15
+    qq = inputs.rhs(4, mesh.n_nodes)
+    yy = torch.empty(prob.N, dtype=torch.float64, device="cuda")
+    dcg.dcg_embed(prob, dev(qq), yy)
+    assert np.array_equal(host(yy), fem.embed(mesh, qq))
+
+
+# --------------------------------------------------------------------------- multigrid pieces
+
+
+def _pair(d, n, dt, o: mg.MGOptions, precision=dcg.DCG_FP64):
+    asm = fem.assemble(d, n, dt)
+    V = fem.V_matrix(asm.mesh)
+    H = mg.Hierarchy(d, n, mg.inner_matrix(V, asm.matrix()), o)
+    prob = dcg.dcg_assemble(d, n, dt)
+    dcg.dcg_setup(prob, gpu_opts(o, precision=precision))
+    return asm, H, prob
+
+
+@pytest.mark.parametrize("d,n", [(2, 32), (2, 20), (3, 8), (3, 12)])
+@pytest.mark.parametrize("dt", [1e-1, 1e-6])
+def test_inner_operator(d, n, dt):
+    asm, H, prob = _pair(d, n, dt, mg_opts())
+    assert prob.levels == H.J
+    z = inputs.rhs(9, asm.mesh.n_nodes)
+    y = torch.empty_like(dev(z))
+    dcg.dcg_inner_apply(prob, dev(z), y)
+    assert relerr(host(y), H.levels[-1].Z @ z) <= 1e-12
+
+
+@pytest.mark.parametrize("d,n,P,o", [(2, 32, 4, 1), (2, 20, 4, 1), (2, 32, 8, 2), (3, 8, 4, 1), (3, 12, 4, 1),
+                                     (2, 24, 3, 1), (2, 16, 1, 0)])
+@pytest.mark.parametrize("weights", ["multiplicity", "restricted"])
+def test_ras_step(d, n, P, o, weights):
+    asm, H, prob = _pair(d, n, 1e-3, mg_opts(patch=P, overlap=o, weights=weights))
+    for k in range(2, H.J + 1):
+        nn = H.levels[k - 1].Z.shape[0]
+        f = inputs.rhs(20 + k, nn)
+        z = inputs.rhs(40 + k, nn)
+        zt = dev(z)
+        dcg.dcg_ras_step(prob, k, dev(f), zt)
+        assert relerr(host(zt), H.ras_step(k, f, z)) <= 1e-11, k
+
+
+@pytest.mark.parametrize("d,n", [(2, 32), (2, 64), (3, 8), (3, 16), (2, 2), (2, 3)])
+def test_coarse_solve(d, n):
+    asm, H, prob = _pair(d, n, 1e-3, mg_opts())
+    nn = H.levels[0].Z.shape[0]
+    f = inputs.rhs(5, nn)
+    z = torch.empty_like(dev(f))
+    dcg.dcg_coarse_solve(prob, dev(f), z)
+    assert relerr(host(z), H.coarse_solve(f)) <= 1e-11
+
+
+@pytest.mark.parametrize("d,n,P,o", [(2, 32, 4, 1), (2, 40, 4, 1), (3, 8, 4, 1), (3, 16, 4, 1), (2, 64, 8, 2)])
+def test_wcycles(d, n, P, o):
+    asm, H, prob = _pair(d, n, 1e-3, mg_opts(patch=P, overlap=o))
+    g = inputs.rhs(13, asm.mesh.n_nodes)
+    for ncyc in [1, 3]:
+        zt = torch.zeros(prob.n_nodes, dtype=torch.float64, device="cuda")
+        dcg.dcg_mg_cycles(prob, dev(g), zt, ncyc)
+        z = np.zeros_like(g)
+        for _ in range(ncyc):
+            z = H.wcycle(g, z)
+        assert relerr(host(zt), z) <= 1e-10, ncyc
+
+
+@pytest.mark.parametrize("d,n", [(2, 32), (3, 8)])
+def test_wcycles_mixed(d, n):
+    asm, H, prob = _pair(d, n, 1e-3, mg_opts(), precision=dcg.DCG_MIXED)
+    g = inputs.rhs(13, asm.mesh.n_nodes)
+    zt = torch.zeros(prob.n_nodes, dtype=torch.float64, device="cuda")
+    dcg.dcg_mg_cycles(prob, dev(g), zt, 1)
+    z = H.wcycle(g, np.zeros_like(g))
+    assert relerr(host(zt), z) <= 1e-5
+    # FP64 residuals make the FP32 cycle converge to FP64 accuracy
+    zt.zero_()
+    ncyc = dcg.dcg_mg_solve(prob, dev(g), zt, 1e-11)
+    zo, no = H.multigrid(g, 1e-11, 100)
+    assert relerr(host(zt), zo) <= 1e-9
+    assert abs(ncyc - no) <= 2
+
+
+@pytest.mark.parametrize("d,n", [(2, 32), (3, 8)])
+def test_mg_solve_counts(d, n):
+    asm, H, prob = _pair(d, n, 1e-3, mg_opts())
+    g = inputs.rhs(17, asm.mesh.n_nodes)
+    for tol in [1e-4, 1e-10]:
+        zt = torch.zeros(prob.n_nodes, dtype=torch.float64, device="cuda")
+        ncyc = dcg.dcg_mg_solve(prob, dev(g), zt, tol)
+        zo, no = H.multigrid(g, tol, 100)
+        assert ncyc == no
+        assert relerr(host(zt), zo) <= 1e-9
+
+
+# --------------------------------------------------------------------------- solves
+
+
+def _solve_pair(d, n, dt, o: mg.MGOptions, rule="fixed", rec="fcg1", c=0.01, precision=dcg.DCG_FP64, seed=0,
+                deflate=True):
+    asm = fem.assemble(d, n, dt)
+    f = inputs.rhs(seed, asm.mesh.n_unknowns)
+    prob = dcg.dcg_assemble(d, n, dt)
+    rules = {"fixed": dcg.DCG_INNER_FIXED, "adaptive": dcg.DCG_INNER_ADAPTIVE, "exact": dcg.DCG_INNER_EXACT}
+    recs = {"fcg1": dcg.DCG_FCG1, "fr": dcg.DCG_FR, "fcg_inf": dcg.DCG_FCG_INF}
+    dcg.dcg_setup(prob, gpu_opts(o, inner_rule=rules[rule], recurrence=recs[rec], c=c, precision=precision,
+                                 deflate=int(deflate)))
+    x = torch.zeros(prob.N, dtype=torch.float64, device="cuda")
+    st = dcg.dcg_solve(prob, dev(f), x, tol=1e-8)
+    if deflate:
+        x_o, st_o = solvers.FDCG(asm, solvers.FDCGOptions(mg=o, inner_rule=rule, recurrence=rec, c=c)).solve(f)
+    else:
+        x_o, st_o = solvers.plain_cg(asm.matrix(), f)
+    return host(x), st, x_o, st_o, asm, f
+
+
+@pytest.mark.parametrize("d,n,dt", [(2, 32, 1e-3), (2, 32, 1e-6), (2, 21, 1e-2), (3, 8, 1e-4), (3, 11, 1e-1)])
+def test_plain_cg(d, n, dt):
+    x, st, x_o, st_o, asm, f = _solve_pair(d, n, dt, mg_opts(), deflate=False)
+    assert st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8
+    assert abs(st["outer_its"] - st_o.outer_its) <= 2
+    assert relerr(x, x_o) <= 1e-7
+
+
+@pytest.mark.parametrize("d,n,dt", [(2, 32, 1e-3), (2, 32, 1e-1), (2, 32, 1e-6), (2, 20, 1e-4), (3, 8, 1e-4),
+                                    (3, 12, 1e-2)])
+@pytest.mark.parametrize("rule", ["fixed", "adaptive", "exact"])
+def test_dcg_fp64(d, n, dt, rule):
+    x, st, x_o, st_o, asm, f = _solve_pair(d, n, dt, mg_opts(), rule=rule)
+    assert st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8, st
+    assert abs(st["outer_its"] - st_o.outer_its) <= 2, (st, st_o.outer_its)
+    if rule != "exact":
+        assert abs(st["total_mg_cycles"] - st_o.total_mg_cycles) <= max(4, 0.05 * st_o.total_mg_cycles)
+    assert relerr(x, x_o) <= 1e-7
+    A = asm.matrix()
+    assert np.linalg.norm(f - A @ x) <= 1e-8 * np.linalg.norm(f)
+
+
+@pytest.mark.parametrize("rec", ["fr", "fcg_inf"])
+def test_dcg_recurrences(rec):
+    x, st, x_o, st_o, asm, f = _solve_pair(2, 32, 1e-4, mg_opts(), rec=rec)
+    assert st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8
+    assert abs(st["outer_its"] - st_o.outer_its) <= 2
+    assert relerr(x, x_o) <= 1e-7
+
+
+@pytest.mark.parametrize("d,n,dt", [(2, 32, 1e-3), (2, 64, 1e-5), (3, 8, 1e-4)])
+def test_dcg_mixed(d, n, dt):
+    x, st, x_o, st_o, asm, f = _solve_pair(d, n, dt, mg_opts(), precision=dcg.DCG_MIXED)
+    assert st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8
+    assert abs(st["outer_its"] - st_o.outer_its) <= 3
+    assert relerr(x, x_o) <= 1e-7
+
+
+def test_dcg_cfg2_patches():
+    """The large-config smoother (8x8 cores, overlap 2) at a size the oracle
+    finishes in seconds."""
+    x, st, x_o, st_o, asm, f = _solve_pair(2, 64, 1e-5, mg_opts(patch=8, overlap=2))
+    assert st["status"] == dcg.DCG_OK and abs(st["outer_its"] - st_o.outer_its) <= 2
+    assert relerr(x, x_o) <= 1e-7
+
+
+# --------------------------------------------------------------------------- edge cases
+
+
+def test_edge_cases():
+    d, n, dt = 2, 16, 1e-3
+    prob = dcg.dcg_assemble(d, n, dt)
+    dcg.dcg_setup(prob, dcg.options())
+    N = prob.N
+    # zero right-hand side
+    x = torch.ones(N, dtype=torch.float64, device="cuda")
+    st = dcg.dcg_solve(prob, torch.zeros(N, dtype=torch.float64, device="cuda"), x)
+    assert st["status"] == dcg.DCG_OK and st["outer_its"] == 0 and not x.any().item()
+    # iteration cap
+    f = dev(inputs.rhs(0, N))
+    x = torch.zeros_like(f)
+    st = dcg.dcg_solve(prob, f, x, tol=1e-12, max_it=3)
+    assert st["status"] == dcg.DCG_ERR_NOT_CONVERGED and st["outer_its"] == 3
+    # warm start from the solution
+    x = torch.zeros_like(f)
+    dcg.dcg_solve(prob, f, x, tol=1e-10)
+    st = dcg.dcg_solve(prob, f, x, tol=1e-10)
+    assert st["outer_its"] <= 1 and st["true_relres"] <= 1e-10
+    # host-array entry point gives the same answer
+    xh = np.zeros(N)
+    st_h = dcg.dcg_solve_host(prob, inputs.rhs(0, N), xh, tol=1e-10)
+    assert st_h["status"] == dcg.DCG_OK and relerr(xh, host(x)) <= 1e-9
+    # invalid options
+    with pytest.raises(dcg.DCGError):
+        dcg.dcg_setup(prob, dcg.options(overlap=9, patch=4))
+    with pytest.raises(dcg.DCGError):
+        dcg.dcg_setup(prob, dcg.options(patch=16, overlap=1))
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_tiny_meshes_dense(n):
+    """Degenerate sizes (one interior node per axis and up): dense solve."""
+    for d in (2, 3):
+        asm = fem.assemble(d, n, 1e-2)
+        f = inputs.rhs(1, asm.mesh.n_unknowns)
+        x_ref = solvers.dense_solve(asm, f)
+        prob = dcg.dcg_assemble(d, n, 1e-2)
+        dcg.dcg_setup(prob, dcg.options())
+        x = torch.zeros(prob.N, dtype=torch.float64, device="cuda")
+        st = dcg.dcg_solve(prob, dev(f), x, tol=1e-12)
+        assert st["status"] == dcg.DCG_OK
+        assert relerr(host(x), x_ref) <= 1e-9
+
+
+def test_batched_matches_single():
+    probs, fs, xs, ref = [], [], [], []
+    for p, (n, dt) in enumerate([(16, 1e-3), (24, 1e-5)]):
+        prob = dcg.dcg_assemble(2, n, dt)
+        dcg.dcg_setup(prob, dcg.options())
+        probs.append(prob)
+        for r in range(2):
+            f = dev(inputs.rhs(0, prob.N, p=p, r=r))
+            fs.append(f)
+            xs.append(torch.zeros_like(f))
+            x1 = torch.zeros_like(f)
+            dcg.dcg_solve(prob, f, x1)
+            ref.append(host(x1))
+    code, stats = dcg.dcg_solve_batched(probs, 2, fs, xs)
+    assert code == dcg.DCG_OK
+    for k in range(4):
+        assert stats[k]["true_relres"] <= 1e-8
+        assert relerr(host(xs[k]), ref[k]) <= 1e-9
