@@ -7,7 +7,9 @@ FDCG follows Algorithm 2 with the outer FCG of Algorithm 1:
 * pi(z, tol) = V * Multigrid(V^T z, tol)                      (Algorithm 2)
 * M_D(z, tol) = A (z - pi(A z, tol))                           (Algorithm 2)
 * f_D = f - A pi(f, tol): reading of the garbled "pi^T(f)"; it is
-  (I - pi_A)^T f, the right-hand side of Eq. defl_sys.
+  (I - pi_A)^T f, the right-hand side of Eq. defl_sys. pi(f, tol) appears
+  in Algorithm 2's f_D line and in its reconstruction line with the same
+  arguments, so it is evaluated once and reused.
 * x_hat = FCG(f_D, x0, M_D); x = x_hat - pi(A x_hat) + pi(f)   (Eq. x_defl)
 * outer stop ||r_i||_2 <= tol ||f||_2 on the recursive deflated residual.
 * inner tolerance, relative to ||V^T t||: fixed tau_c = c_F * tol (Eq.
@@ -139,7 +141,10 @@ class FDCG:
     def _pass(self, f, x0, eps, tol, max_it, st: SolveStats):
         A, o = self.A, self.opts
         tc0 = o.c * tol
-        f_D = f - A @ self.pi(f, tc0, st)
+        # pi(f, tol) enters Algorithm 2 twice (f_D and the reconstruction)
+        # with the same arguments; it is evaluated once.
+        pi_f = self.pi(f, tc0, st)
+        f_D = f - A @ pi_f
         if x0 is None:
             xh = np.zeros_like(f)
             r = f_D.copy()
@@ -183,7 +188,7 @@ class FDCG:
             else:
                 raise ValueError(o.recurrence)
             rr = rr_new
-        x = xh - self.pi(A @ xh, tc0, st) + self.pi(f, tc0, st)
+        x = xh - self.pi(A @ xh, tc0, st) + pi_f
         return x, conv
 
     def solve(self, f: np.ndarray, tol: float = 1e-8, max_it: int = 100000, x0=None):
