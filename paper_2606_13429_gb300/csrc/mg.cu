@@ -247,7 +247,7 @@ __device__ __forceinline__ T stencil_apply(const Stencil<T>& st, const T* __rest
       for (int dx = -1; dx <= 1; ++dx) {
         const int xc = c[0] + dx;
         if (xc < 0 || xc >= m) continue;
-        const T w = st.c[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+        const T w = st.c[(dx + 1) + 3 * (dy + 1) + (D > 2 ? 9 * (dz + 1) : 0)];
         acc += w * z[xc + (long long)m * yc + (D > 2 ? mm * zc : 0)];
       }
     }
@@ -786,10 +786,25 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
   if (D == 2) k_zj_rows<2><<<g, 256, 0, s>>>(p->row_ptr, p->col_idx, p->vals, p->m, p->n_nodes, 1.0 / D, rows, scal2);
   else k_zj_rows<3><<<g, 256, 0, s>>>(p->row_ptr, p->col_idx, p->vals, p->m, p->n_nodes, 1.0 / D, rows, scal2);
   DCG_LAUNCH_CHECK();
-  const int mid = p->m / 2;
-  const long long ref = mid + (long long)p->m * mid + (D > 2 ? (long long)p->m * p->m * mid : 0);
+  // Reference stencil: offset o is read from a node whose neighbour at o
+  // exists (low corner for +1, high corner for -1), so meshes with fewer than
+  // three interior nodes per axis are covered too; offsets that exist for no
+  // node (m = 1) stay zero and are never used.
   double* d_ref = scal2 + 2;
-  DCG_CUDA(cudaMemcpyAsync(d_ref, rows + ref * 27, sizeof(double) * 27, cudaMemcpyDeviceToDevice, s));
+  DCG_CUDA(cudaMemsetAsync(d_ref, 0, sizeof(double) * 27, s));
+  for (int o = 0; o < (D == 2 ? 9 : 27); ++o) {
+    const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, D > 2 ? o / 9 - 1 : 0};
+    long long node = 0, stride = 1;
+    bool exists = true;
+    for (int k = 0; k < D; ++k) {
+      const int c = off[k] > 0 ? 0 : (off[k] < 0 ? p->m - 1 : 0);
+      exists = exists && (c + off[k] >= 0 && c + off[k] < p->m);
+      node += c * stride;
+      stride *= p->m;
+    }
+    if (exists)
+      DCG_CUDA(cudaMemcpyAsync(d_ref + o, rows + node * 27 + o, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
   if (D == 2) k_zj_check<2><<<g, 256, 0, s>>>(rows, d_ref, p->m, p->n_nodes, scal2 + 1);
   else k_zj_check<3><<<g, 256, 0, s>>>(rows, d_ref, p->m, p->n_nodes, scal2 + 1);
   DCG_LAUNCH_CHECK();
@@ -844,7 +859,11 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
     Level& L1 = p->levels[0];
     Stencil<double> cf = q1_laplacian_over_d(D, 1.0 / L1.n);
     double dev = 0.0, mx = 0.0;
-    for (int k = 0; k < 27; ++k) {
+    for (int k = 0; k < (D == 2 ? 9 : 27); ++k) {
+      const int off[3] = {k % 3 - 1, (k / 3) % 3 - 1, D > 2 ? k / 9 - 1 : 0};
+      bool used = true;  // offsets reaching outside a 1-node grid never act
+      for (int a = 0; a < D; ++a) used = used && (off[a] == 0 || L1.m >= 2);
+      if (!used) continue;
       dev = std::max(dev, std::fabs(cf.c[k] - L1.st64.c[k]));
       mx = std::max(mx, std::fabs(cf.c[k]));
     }
