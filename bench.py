@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of the deflated-CG hot path on one GB300 (or N replicas).
+
+Workload (default): 2D unit square, 1024 x 1024 Q1 pseudo-stress elements
+(N = 4,186,116 unknowns, BSR 4x4, 9 blocks per row), nu = 1, right-hand side
+uniform[-1, 1) from seed 0, solved to true relative residual 1e-8 (FP64) for
+each dt in {1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 1e-1}. One step = one complete
+deflated-CG solve (W-cycle multigrid with RAS 8x8 cores, overlap 2, 2+2
+smoothing steps, 4 levels; FCG(1) outer; fixed inner tolerance c_F = 0.01)
+at the next dt of the sweep. The headline runs the W-cycle in FP32 and
+everything else in FP64 (--precision fp64 runs all in FP64).
+
+Printed: one JSON line (rank 0) with the contract keys, plus "roofline"
+(dominant kernel class, measured live with CUDA events during the timed
+steps), "cpu_baseline" (the FP64 oracle on the host: one SpMV and one
+W-cycle at this size, composed with the iteration counts of the timed
+solves), "e2e" (same solves through the host-array entry point, copies
+included), "clocks" (nvidia-smi samples during the timed region) and
+"extra" (per-dt iterations and times, plain CG, kernel breakdown).
+
+--impl reference times the oracle alone on a bounded sample of the same
+workload (one SpMV and one W-cycle per step), scaled to seconds per solve
+with the outer/inner iteration counts this bench measured on GB300.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+DTS = [1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 1e-1]
+WORKLOAD = ("2D unit square 1024x1024 Q1 pseudo-stress (4 comps/node, N=4,186,116, BSR 4x4 FP64), nu=1, "
+            "dt sweep 1e-6..1e-1 (one dt per step), RHS uniform[-1,1) seed 0, tol 1e-8 true residual; "
+            "DCG: FCG(1), c_F=0.01, W-cycle 4 levels, RAS 8x8 cores overlap 2, m1=m2=2")
+# Outer / in-iteration W-cycle counts per dt of this workload (mixed precision),
+# measured on GB300 by this bench; the parity tests hold device and oracle
+# counts within +-2 at sizes the oracle finishes. Used only to scale the
+# oracle's per-kernel timings to seconds per solve in the reference arm.
+REF_COUNTS = {1e-6: (34, 170), 1e-5: (60, 300), 1e-4: (335, 1675), 1e-3: (1000, 5000),
+              1e-2: (3200, 16000), 1e-1: (7500, 37500)}
+
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- distributed
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------- oracle timing
+
+
+def oracle_kernel_times(n=1024, P=8, o=2, dt=1e-6):
+    """Time the FP64 oracle at the bench size: one BSR SpMV and one W-cycle
+    (single thread). Returns seconds for each and the sample description."""
+    from oracle import fem, mg
+    from paper_2606_13429_gb300 import inputs
+    asm = fem.assemble(2, n, dt)
+    A = asm.matrix().tocsr()
+    V = fem.V_matrix(asm.mesh)
+    H = mg.Hierarchy(2, n, mg.inner_matrix(V, A), mg.MGOptions(patch=P, overlap=o, m1=2, m2=2, max_levels=4))
+    x = inputs.rhs(0, asm.mesh.n_unknowns)
+    g = inputs.rhs(1, asm.mesh.n_nodes)
+    t0 = time.perf_counter()
+    y = A @ x
+    t_spmv = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    z = H.wcycle(g, np.zeros_like(g))
+    t_wc = time.perf_counter() - t0
+    del y, z
+    return t_spmv, t_wc
+
+
+def compose_solve_time(t_spmv, t_wc, counts, n_unknowns):
+    """Seconds per solve from per-kernel times: per outer iteration two SpMVs
+    and its W-cycles, plus about ten vector passes; the f_D and reconstruction
+    inner solves add ~2 inner solves of W-cycles and two SpMVs."""
+    t_vec = 10 * n_unknowns * 8 / 5e9  # ~5 GB/s single-thread numpy streaming
+    total = 0.0
+    for outer, cycles in counts:
+        inner = cycles / max(1, outer)
+        total += outer * (2 * t_spmv + t_vec) + cycles * t_wc + 2 * (inner * t_wc + t_spmv)
+    return total / len(counts)
+
+
+# --------------------------------------------------------------------------- main arm
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2606_13429_gb300 import build as B
+    from paper_2606_13429_gb300 import dcg, inputs
+
+    ws, rank, local = dist_init()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    B.build()
+    dcg.load()
+    prec = dcg.DCG_MIXED if args.precision == "mixed" else dcg.DCG_FP64
+    opts = dcg.options(patch=8, overlap=2, m1=2, m2=2, max_levels=4, precision=prec, inner_rule=dcg.DCG_INNER_FIXED,
+                       c=0.01, recurrence=dcg.DCG_FCG1)
+    n = args.n
+    probs = {}
+    for dt in DTS:
+        p = dcg.dcg_assemble(2, n, dt)
+        dcg.dcg_setup(p, opts)
+        probs[dt] = p
+    N = probs[DTS[0]].N
+    f = torch.from_numpy(inputs.rhs(0, N)).cuda()
+    x = torch.zeros_like(f)
+    stream = torch.cuda.current_stream()
+
+    def step(k, record=None):
+        dt = DTS[k % len(DTS)]
+        x.zero_()
+        st = dcg.dcg_solve(probs[dt], f, x, tol=1e-8, max_it=args.max_it)
+        if record is not None:
+            record.append((dt, st))
+        return st
+
+    # warm-up: every class timed, to find the dominant one
+    for p in probs.values():
+        dcg.dcg_profile_enable(p, dcg.PROF_CLASSES)
+    warm = []
+    for k in range(args.warmup):
+        step(k, warm)
+    breakdown = {c: {"ms": 0.0, "launches": 0, "flops": 0.0, "bytes": 0.0} for c in dcg.PROF_CLASSES}
+    for p in probs.values():
+        r = dcg.dcg_profile_read(p)
+        for c in dcg.PROF_CLASSES:
+            for key in breakdown[c]:
+                breakdown[c][key] += r[c][key]
+    dominant = max(breakdown, key=lambda c: breakdown[c]["ms"])
+    for p in probs.values():
+        dcg.dcg_profile_enable(p, [dominant])
+
+    # timed region
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = dcg.dcg_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    timed = []
+    for k in range(args.steps):
+        step(k, timed)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    launches = dcg.dcg_kernel_launches() - launches0
+    clk = clocks.stop() if rank == 0 else None
+    elapsed_ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+    dom = {"ms": 0.0, "launches": 0, "flops": 0.0, "bytes": 0.0}
+    for p in probs.values():
+        r = dcg.dcg_profile_read(p)[dominant]
+        for key in dom:
+            dom[key] += r[key]
+        dcg.dcg_profile_enable(p, [])
+    ok = all(st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8 for _, st in timed)
+
+    # end to end: host arrays in pinned memory, copies inside the timed region
+    f_h = torch.from_numpy(inputs.rhs(0, N)).pin_memory()
+    x_h = torch.zeros(N, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    e2e_stats = []
+    for k in range(args.steps):
+        dt = DTS[k % len(DTS)]
+        x_h.zero_()
+        e2e_stats.append(dcg.dcg_solve_host(probs[dt], f_h, x_h, tol=1e-8, max_it=args.max_it))
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - e0) / args.steps
+
+    # plain CG, FP64, at each dt (reported, outside the timed region)
+    extra = {"per_dt": {}}
+    if not args.skip_cg:
+        copt = dcg.options(deflate=0)
+        for dt in DTS:
+            pc = dcg.dcg_assemble(2, n, dt)
+            dcg.dcg_setup(pc, copt)
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = dcg.dcg_solve(pc, f, x, tol=1e-8, max_it=args.max_it)
+            torch.cuda.synchronize()
+            extra["per_dt"].setdefault(str(dt), {})["plain_cg"] = {
+                "s": time.perf_counter() - t0, "outer_its": st["outer_its"], "true_relres": st["true_relres"]}
+            pc.close()
+    for dt, st in timed:
+        extra["per_dt"].setdefault(str(dt), {})["dcg"] = {
+            "s": st["solve_ms"] / 1e3, "outer_its": st["outer_its"], "total_mg_cycles": st["total_mg_cycles"],
+            "avg_inner": round(st["avg_inner"], 2), "true_relres": st["true_relres"], "restarts": st["restarts"]}
+
+    # SpMV bandwidth on this operator (FP64, plain product)
+    p0 = probs[DTS[0]]
+    dcg.dcg_profile_enable(p0, ["spmv"])
+    y = torch.empty_like(f)
+    for _ in range(20):
+        dcg.dcg_spmv(p0, f, y)
+    sp = dcg.dcg_profile_read(p0)["spmv"]
+    dcg.dcg_profile_enable(p0, [])
+    extra["spmv_fp64"] = {"GB_per_s": sp["bytes"] / (sp["ms"] / 1e3) / 1e9, "ms": sp["ms"] / max(1, sp["launches"])}
+    extra["kernel_breakdown_warmup_ms"] = {c: round(v["ms"], 3) for c, v in breakdown.items()}
+
+    peaks, peak_src = load_peaks()
+    roof = roofline(dominant, dom, peaks, peak_src)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        t_spmv, t_wc = oracle_kernel_times(n)
+        counts = [(st["outer_its"], st["iter_mg_cycles"]) for _, st in timed]
+        cpu = {"value": compose_solve_time(t_spmv, t_wc, counts, N), "unit": "s/solve", "cores": 1,
+               "kind": "oracle",
+               "sample": "FP64 oracle at 1024^2 on the host: one BSR SpMV (%.3f s) and one W-cycle (%.2f s), "
+                         "single thread, composed with the outer/inner iteration counts of the timed solves"
+                         % (t_spmv, t_wc)}
+
+    if rank == 0:
+        value = elapsed_ms / 1e3 / args.steps
+        line = {
+            "metric": "time-to-1e-8 true residual, deflated CG (W-cycle MG + RAS inner), 2D Q1 pseudo-stress 1024^2, "
+                      "dt sweep 1e-6..1e-1",
+            "value": value, "unit": "s/solve", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64 outer CG, f32 W-cycle" if prec == dcg.DCG_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (BSR matrix 1.2 GB per dt)", "precision": args.precision,
+                       "all_converged": ok},
+            "e2e": {"value": e2e_s, "unit": "s/solve", "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": N * 8},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "extra": extra,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2606_13429_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def roofline(dominant, dom, peaks, peak_src):
+    """Roofline of the dominant kernel class over the timed region."""
+    secs = dom["ms"] / 1e3
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            tr = json.load(fh)
+        ent = tr.get(dominant)
+        if ent and ent.get("source_hash") == kernel_source_hash():
+            traffic = ent["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    if dominant in ("spmv", "vec", "ras_update", "transfer", "inner_res") or secs <= 0:
+        achieved = dom["bytes"] / secs / 1e9 if secs > 0 else 0.0
+        peak = peaks["hbm_gbs"]
+        return {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src + " copy bandwidth",
+                "launches": dom["launches"],
+                "algorithmic_bytes_per_launch": dom["bytes"] / max(1, dom["launches"])}
+    # FP32 SIMT products (RAS patch inverses, coarse passes): plain ALU bound
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    achieved = dom["flops"] / secs / 1e12
+    return {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x %.0f MHz (max SM clock)" % mhz,
+            "launches": dom["launches"], "algorithmic_flops_per_launch": dom["flops"] / max(1, dom["launches"])}
+
+
+# --------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    ws, rank, local = dist_init()
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    samples = []
+    for k in range(args.warmup + args.steps):
+        t_spmv, t_wc = oracle_kernel_times(args.n)
+        if k >= args.warmup:
+            samples.append((t_spmv, t_wc))
+    t_spmv = statistics.median(s[0] for s in samples)
+    t_wc = statistics.median(s[1] for s in samples)
+    counts = [REF_COUNTS[DTS[k % len(DTS)]] for k in range(args.steps)]
+    N = 4 * (args.n - 1) ** 2
+    value = compose_solve_time(t_spmv, t_wc, counts, N)
+    sample = ("FP64 oracle at 1024^2, single thread: per step one BSR SpMV and one W-cycle (medians %.3f s, %.2f s), "
+              "scaled to seconds per solve with the sweep's outer/inner iteration counts" % (t_spmv, t_wc))
+    line = {
+        "metric": "time-to-1e-8 true residual, deflated CG (W-cycle MG + RAS inner), 2D Q1 pseudo-stress 1024^2, "
+                  "dt sweep 1e-6..1e-1",
+        "value": value, "unit": "s/solve", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": (time.perf_counter() - t0) * 1e3 / (args.steps + args.warmup),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": "host oracle"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "s/solve", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--max-it", type=int, default=20000)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-cg", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -198,6 +198,31 @@ int dcg_ras_step(dcg_problem* p, int level, const double* f_dev, double* z_dev, 
 /* Exact coarsest-level solve z = Z_1^-1 f (FP64 arrays of level-1 size). */
 int dcg_coarse_solve(dcg_problem* p, const double* f_dev, double* z_dev, void* stream);
 
+/* ---- timing of kernel classes (CUDA events, off by default) ----------- */
+#define DCG_PROF_SPMV        0  /* BSR products (all fused variants) */
+#define DCG_PROF_VEC         1  /* vector updates and reductions */
+#define DCG_PROF_RAS_SOLVE   2  /* RAS residual + shared-inverse products */
+#define DCG_PROF_RAS_UPDATE  3  /* RAS weighted combination */
+#define DCG_PROF_TRANSFER    4  /* level residual, restriction, prolongation */
+#define DCG_PROF_COARSE      5  /* coarsest exact solve */
+#define DCG_PROF_INNER_RES   6  /* FP64 inner residual of Algorithm 3 */
+
+/* Enable timing for the classes whose bits are set in `mask` (bit c for
+ * class c; 0 disables) and reset the accumulators. Launches of those classes
+ * are bracketed by CUDA events on their stream (inside the W-cycle graph as
+ * event-record nodes); the graph is rebuilt when the mask changes. */
+int dcg_profile_enable(dcg_problem* p, unsigned mask, void* stream);
+
+/* Accumulated device time (ms), launch count and algorithmic flops / bytes
+ * (the work the method requires, not hardware counters) of one class since
+ * dcg_profile_enable. Synchronises `stream`. */
+int dcg_profile_read(dcg_problem* p, int cls, double* ms, long long* launches, double* flops, double* bytes,
+                     void* stream);
+
+/* Number of kernels this library has launched in the process so far (a
+ * replay of the captured W-cycle graph counts each of its kernel nodes). */
+long long dcg_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

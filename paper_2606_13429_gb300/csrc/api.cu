@@ -9,6 +9,8 @@
 
 namespace dcg {
 
+long long g_launch_count = 0;
+
 namespace {
 thread_local std::string g_err;
 }
@@ -28,7 +30,7 @@ long long ipow_ll(long long b, int e) {
 
 int check_options(const dcg_options* o, int dim) {
   if (!o) return DCG_ERR_INVALID_ARG;
-  bool ok = o->max_levels >= 1 && o->patch >= 1 && o->overlap >= 0 && o->overlap <= o->patch && o->m1 >= 0 &&
+  bool ok = o->max_levels >= 1 && o->patch >= 1 && o->overlap >= 0 && 2 * o->overlap <= o->patch && o->m1 >= 0 &&
             o->m2 >= 0 && (o->inner_rule >= 0 && o->inner_rule <= 2) && o->c > 0 && o->inner_nmax >= 1 &&
             (o->recurrence >= 0 && o->recurrence <= 2) && (o->precision == DCG_FP64 || o->precision == DCG_MIXED) &&
             (o->ras_inverse == DCG_INV_FP32 || o->ras_inverse == DCG_INV_BF16) &&
@@ -59,6 +61,80 @@ int alloc_vec(double** v, long long n) {
 }
 
 }  // namespace
+
+cudaEvent_t prof_event(dcg_problem* p) {
+  Prof& P = p->prof;
+  if (!P.pool.empty()) {
+    cudaEvent_t e = P.pool.back();
+    P.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int prof_begin(dcg_problem* p, int cls, cudaStream_t s, bool capture) {
+  Prof& P = p->prof;
+  if (!(P.mask & (1u << cls))) return -1;
+  ProfPair pr;
+  pr.a = prof_event(p);
+  pr.b = prof_event(p);
+  pr.cls = cls;
+  if (capture) {
+    cudaEventRecordWithFlags(pr.a, s, cudaEventRecordExternal);
+    P.graph.push_back(pr);
+    return (int)P.graph.size() - 1;
+  }
+  cudaEventRecord(pr.a, s);
+  P.pending.push_back(pr);
+  return (int)P.pending.size() - 1;
+}
+
+void prof_end(dcg_problem* p, int idx, cudaStream_t s, double flops, double bytes, bool capture) {
+  if (idx < 0) return;
+  Prof& P = p->prof;
+  ProfPair& pr = capture ? P.graph[idx] : P.pending[idx];
+  pr.flops = flops;
+  pr.bytes = bytes;
+  if (capture) cudaEventRecordWithFlags(pr.b, s, cudaEventRecordExternal);
+  else cudaEventRecord(pr.b, s);
+}
+
+static void prof_account(Prof& P, const ProfPair& pr) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, pr.a, pr.b) == cudaSuccess) {
+    P.ms[pr.cls] += ms;
+    P.flops[pr.cls] += pr.flops;
+    P.bytes[pr.cls] += pr.bytes;
+    P.launches[pr.cls] += 1;
+  }
+}
+
+void prof_flush(dcg_problem* p) {
+  Prof& P = p->prof;
+  for (auto& pr : P.pending) {
+    prof_account(P, pr);
+    P.pool.push_back(pr.a);
+    P.pool.push_back(pr.b);
+  }
+  P.pending.clear();
+}
+
+void prof_flush_graph(dcg_problem* p) {
+  Prof& P = p->prof;
+  for (auto& pr : P.graph) prof_account(P, pr);
+}
+
+void prof_clear_graph(dcg_problem* p) {
+  Prof& P = p->prof;
+  for (auto& pr : P.graph) {
+    P.pool.push_back(pr.a);
+    P.pool.push_back(pr.b);
+  }
+  P.graph.clear();
+}
+
 }  // namespace dcg
 
 using namespace dcg;
@@ -258,6 +334,9 @@ int dcg_solve_batched(int nprob, dcg_problem* const* probs, int nrhs, const doub
 void dcg_destroy(dcg_problem* p) {
   if (!p) return;
   mg_free(p);
+  prof_flush(p);
+  prof_clear_graph(p);
+  for (cudaEvent_t e : p->prof.pool) cudaEventDestroy(e);
   free_solver_buffers(p);
   cudaFree(p->row_ptr);
   cudaFree(p->col_idx);
@@ -338,5 +417,35 @@ int dcg_coarse_solve(dcg_problem* p, const double* f, double* z, void* stream) {
   if (!p->is_setup || p->levels.empty()) return DCG_ERR_STATE;
   return mg_coarse_hook(p, f, z, (cudaStream_t)stream);
 }
+
+int dcg_profile_enable(dcg_problem* p, unsigned mask, void* stream) {
+  if (!p) return DCG_ERR_INVALID_ARG;
+  DCG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  prof_flush(p);
+  Prof& P = p->prof;
+  for (int c = 0; c < PC_COUNT; ++c) {
+    P.ms[c] = P.flops[c] = P.bytes[c] = 0.0;
+    P.launches[c] = 0;
+  }
+  const bool rebuild = P.mask != mask;
+  P.mask = mask;
+  if (rebuild && p->is_setup) return mg_rebuild_graph(p);
+  return DCG_OK;
+}
+
+int dcg_profile_read(dcg_problem* p, int cls, double* ms, long long* launches, double* flops, double* bytes,
+                     void* stream) {
+  if (!p || cls < 0 || cls >= PC_COUNT) return DCG_ERR_INVALID_ARG;
+  DCG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  prof_flush(p);
+  const Prof& P = p->prof;
+  if (ms) *ms = P.ms[cls];
+  if (launches) *launches = P.launches[cls];
+  if (flops) *flops = P.flops[cls];
+  if (bytes) *bytes = P.bytes[cls];
+  return DCG_OK;
+}
+
+long long dcg_kernel_launches(void) { return g_launch_count; }
 
 }  // extern "C"

@@ -28,7 +28,15 @@ void set_error_msg(const std::string& msg);
     if (s__ != DCG_OK) return s__; \
   } while (0)
 
-#define DCG_LAUNCH_CHECK() DCG_CUDA(cudaGetLastError())
+// Every kernel launch is followed by DCG_LAUNCH_CHECK(), which also counts it
+// (launches captured into the W-cycle graph are counted per replay instead).
+extern long long g_launch_count;
+inline void note_launches(long long n) { g_launch_count += n; }
+#define DCG_LAUNCH_CHECK()                 \
+  do {                                     \
+    ::dcg::g_launch_count++;               \
+    DCG_CUDA(cudaGetLastError());          \
+  } while (0)
 
 constexpr int kMaxDim = 3;
 constexpr int kRedThreads = 256;
@@ -128,6 +136,7 @@ struct Tiles1D {
 struct RasClass {
   int len[kMaxDim];   // box extent per axis
   int np;             // prod(len)
+  int local_off;      // offset of the class's packed local coordinates
   long long inv_off;  // offset of the inverse in the level's inverse array
 };
 
@@ -145,8 +154,13 @@ struct Level {
   int* d_work = nullptr;            // [nwork * 3] (class, first index into d_class_patches, count)
   int* d_class_patches = nullptr;   // patch ids grouped by class
   RasClass* d_classes = nullptr;
+  int4* d_origin = nullptr;         // [npatch] box origin coordinates and node
+  int* d_local = nullptr;           // packed local coordinates of every class
+  int4* d_axis_tab = nullptr;       // [m] boxes containing each coordinate
+  int* d_axis_len = nullptr;        // [ntile] box extent per tile
   int nwork = 0;
   long long ylen = 0;
+  long long ras_np2 = 0;            // sum over boxes of np^2 (FMAs of one smoothing product)
   void* d_inv = nullptr;            // inverses in the W-cycle precision (row-major, symmetric)
   void* d_inv_bf16 = nullptr;       // optional BF16 copy
   // vectors in the W-cycle precision
@@ -171,6 +185,29 @@ struct SolverBuffers {
   double* qdirs = nullptr; // FCG(inf): [ndir][N] M_D directions
   double* coef = nullptr;  // FCG(inf): [ndir] coefficients
   int ndir_cap = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Optional per-kernel-class timing with CUDA events (off by default). Direct
+// launches record an event pair on their stream; launches inside the
+// captured W-cycle graph carry external event-record nodes, read after each
+// graph replay.
+// ---------------------------------------------------------------------------
+enum ProfClass {
+  PC_SPMV = 0, PC_VEC, PC_RAS_SOLVE, PC_RAS_UPDATE, PC_TRANSFER, PC_COARSE, PC_INNER_RES, PC_COUNT
+};
+struct ProfPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  int cls = 0;
+  double flops = 0, bytes = 0;
+};
+struct Prof {
+  unsigned mask = 0;               // bit per ProfClass
+  std::vector<cudaEvent_t> pool;
+  std::vector<ProfPair> pending;   // direct launches since the last flush
+  std::vector<ProfPair> graph;     // pairs inside the W-cycle graph
+  double ms[PC_COUNT] = {}, flops[PC_COUNT] = {}, bytes[PC_COUNT] = {};
+  long long launches[PC_COUNT] = {};
 };
 
 }  // namespace dcg
@@ -198,6 +235,7 @@ struct dcg_problem {
   dcg::SolverBuffers sb;
   double* fine_f64 = nullptr;      // staging for host-array solves (N)
   double* fine_x64 = nullptr;
+  dcg::Prof prof;
 };
 
 namespace dcg {
@@ -221,6 +259,14 @@ inline int grid_for(long long n, int threads, int cap = kMaxRedCtas) {
   if (g > cap) g = cap;
   return (int)g;
 }
+
+// profiling (api.cu): prof_begin returns a pair index or -1 when the class
+// is not profiled; capture = true inside W-cycle graph capture.
+int prof_begin(dcg_problem* p, int cls, cudaStream_t s, bool capture = false);
+void prof_end(dcg_problem* p, int idx, cudaStream_t s, double flops, double bytes, bool capture = false);
+void prof_flush(dcg_problem* p);        // after a synchronisation of the stream
+void prof_flush_graph(dcg_problem* p);  // after a synchronised W-cycle replay
+void prof_clear_graph(dcg_problem* p);
 
 // launchers implemented in the .cu files
 int assemble_device(dcg_problem* p, const double* nu_elem_host, cudaStream_t s);
@@ -249,6 +295,7 @@ int read_scalars(dcg_problem* p, cudaStream_t s);
 
 // multigrid
 int mg_setup(dcg_problem* p, cudaStream_t s);
+int mg_rebuild_graph(dcg_problem* p);
 void mg_free(dcg_problem* p);
 int mg_inner_apply(dcg_problem* p, const double* z, double* y, cudaStream_t s);
 int mg_cycles(dcg_problem* p, const double* g, double* z, int ncycles, cudaStream_t s);

@@ -320,61 +320,72 @@ __global__ void k_prolong_add(const T* __restrict__ coarse, T* __restrict__ fine
 }
 
 struct RasArgs {
-  int m, ntile, P, o;
-  const int* work;           // [nwork*3]
-  const int* class_patches;  // grouped patch ids
+  int m;
+  const int* work;           // [nwork*3]: class, first index into class_patches, count
+  const int* class_patches;  // patch ids grouped by class
   const RasClass* classes;
-  const long long* yoff;     // [npatch]
+  const long long* yoff;     // [npatch] offset of the box's results in y
+  const int4* origin;        // [npatch] box origin (x, y, z) and its node index
+  const int* local;          // per class: packed local coordinates, 10 bits per axis
+  const int4* axis_tab;      // [m] per coordinate: (t0, l0, t1, l1) boxes containing it, -1 = none
+  const int* axis_len;       // [ntile] box extent per tile along an axis
+  int ntile;
   int nwork;
+  int items_per_cta;
+  long long g_off;           // elements of shared memory before the residual tile
 };
 
 // (1) residual on each box of a batch, times the shared inverse, to y.
-template <typename T, int D>
+// A CTA walks a contiguous range of work items (sorted by class) and keeps
+// the class inverse in shared memory while the class does not change.
+template <typename T, int D, bool RESIDENT>
 __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, Stencil<T> st, const T* __restrict__ f,
                                                             const T* __restrict__ z, const T* __restrict__ inv,
                                                             T* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* G = reinterpret_cast<T*>(smem_raw);            // [npmax][kNB]
   const int tid = threadIdx.x;
-  const int tx = tid & 7;   // patch group (4 patches each)
-  const int ty = tid >> 3;  // row group
-  const Tiles1D tl{ra.m, ra.P, ra.o, ra.ntile};
-  for (int w = blockIdx.x; w < ra.nwork; w += gridDim.x) {
+  const int tx = tid & 7;   // group of 4 boxes
+  const int ty = tid >> 3;  // rows ty, ty+32, ...
+  const int w0 = blockIdx.x * ra.items_per_cta;
+  const int w1 = min(ra.nwork, w0 + ra.items_per_cta);
+  int cur_cls = -1;
+  for (int w = w0; w < w1; ++w) {
     const int cls = ra.work[3 * w], first = ra.work[3 * w + 1], nb = ra.work[3 * w + 2];
     const RasClass C = ra.classes[cls];
     const int np = C.np;
-    T* As = G + (size_t)np * kNB;                    // [kKC][np]
+    T* As = reinterpret_cast<T*>(smem_raw);                 // RESIDENT: [np][np], else [kKC][np]
+    T* G = As + ra.g_off;                                   // [np][kNB]
     __syncthreads();
-    // gather residuals: patch fastest
+    if (RESIDENT && cls != cur_cls) {
+      const T* src = inv + C.inv_off;
+      for (int idx = tid; idx < np * np; idx += blockDim.x) As[idx] = src[idx];
+      cur_cls = cls;
+    }
+    // gather residuals f - Z z on the boxes (box index fastest)
     for (int idx = tid; idx < np * kNB; idx += blockDim.x) {
       const int b = idx % kNB, k = idx / kNB;
       T r = 0;
       if (b < nb) {
         const int pid = ra.class_patches[first + b];
-        int t3[3] = {pid % ra.ntile, (pid / ra.ntile) % ra.ntile, D > 2 ? pid / (ra.ntile * ra.ntile) : 0};
-        int lk[3] = {k % C.len[0], (k / C.len[0]) % C.len[1], D > 2 ? k / (C.len[0] * C.len[1]) : 0};
-        int c[3];
-        for (int q = 0; q < 3; ++q) c[q] = (q < D) ? tl.ext_lo(t3[q]) + lk[q] : 0;
-        const long long a = c[0] + (long long)ra.m * c[1] + (D > 2 ? (long long)ra.m * ra.m * c[2] : 0);
+        const int4 o4 = ra.origin[pid];
+        const int pk = ra.local[C.local_off + k];
+        int c[3] = {o4.x + (pk & 1023), o4.y + ((pk >> 10) & 1023), o4.z + ((pk >> 20) & 1023)};
+        const long long a = (long long)o4.w + (pk & 1023) + (long long)ra.m * (((pk >> 10) & 1023) +
+                            (D > 2 ? (long long)ra.m * ((pk >> 20) & 1023) : 0));
         r = f[a] - stencil_apply<T, D>(st, z, ra.m, c);
       }
       G[(size_t)k * kNB + b] = r;
     }
-    // GEMM: Y[i][b] = sum_k inv[i][k] G[k][b]; inv symmetric, row k = column k
     constexpr int RI = kMaxNp / 32;
     T acc[RI][4];
 #pragma unroll
     for (int r = 0; r < RI; ++r)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[r][c] = 0;
-    const T* invc = inv + C.inv_off;
-    for (int k0 = 0; k0 < np; k0 += kKC) {
-      const int kc = min(kKC, np - k0);
+    if (RESIDENT) {
       __syncthreads();
-      for (int idx = tid; idx < kc * np; idx += blockDim.x) As[idx] = invc[(size_t)k0 * np + idx];
-      __syncthreads();
-      for (int kk = 0; kk < kc; ++kk) {
-        const T* g = G + (size_t)(k0 + kk) * kNB + 4 * tx;
+      for (int kk = 0; kk < np; ++kk) {
+        const T* g = G + (size_t)kk * kNB + 4 * tx;
         const T g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3];
         const T* arow = As + (size_t)kk * np;
 #pragma unroll
@@ -386,6 +397,30 @@ __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, Stencil<T
             acc[r][1] += av * g1;
             acc[r][2] += av * g2;
             acc[r][3] += av * g3;
+          }
+        }
+      }
+    } else {
+      const T* invc = inv + C.inv_off;
+      for (int k0 = 0; k0 < np; k0 += kKC) {
+        const int kc = min(kKC, np - k0);
+        __syncthreads();
+        for (int idx = tid; idx < kc * np; idx += blockDim.x) As[idx] = invc[(size_t)k0 * np + idx];
+        __syncthreads();
+        for (int kk = 0; kk < kc; ++kk) {
+          const T* g = G + (size_t)(k0 + kk) * kNB + 4 * tx;
+          const T g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3];
+          const T* arow = As + (size_t)kk * np;
+#pragma unroll
+          for (int r = 0; r < RI; ++r) {
+            const int i = ty + 32 * r;
+            if (i < np) {
+              const T av = arow[i];
+              acc[r][0] += av * g0;
+              acc[r][1] += av * g1;
+              acc[r][2] += av * g2;
+              acc[r][3] += av * g3;
+            }
           }
         }
       }
@@ -405,53 +440,78 @@ __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, Stencil<T
   }
 }
 
-// (2) z[j] += D_j * sum over boxes containing j of y_box[local(j)]
+// (2) z[j] += D_j * sum over boxes containing j of y_box[local(j)], with the
+// boxes found from per-coordinate tables (no integer division).
 template <typename T, int D>
 __global__ void k_ras_update(RasArgs ra, const T* __restrict__ y, T* __restrict__ z, long long nn, int restricted) {
-  const Tiles1D tl{ra.m, ra.P, ra.o, ra.ntile};
   for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nn; a += (long long)gridDim.x * blockDim.x) {
     int c[3];
     coords_of<D>(a, ra.m, c);
-    int tlist[3][3], nt[3];
+    int tl[3][2], ll[3][2], nt[3];
+#pragma unroll
     for (int q = 0; q < 3; ++q) {
-      nt[q] = 0;
-      if (q >= D) { tlist[q][0] = 0; nt[q] = 1; continue; }
-      const int t0 = c[q] / ra.P;
-      for (int t = t0 - 1; t <= t0 + 1; ++t) {
-        if (t < 0 || t >= ra.ntile) continue;
-        if (restricted && t != t0) continue;
-        if (c[q] >= tl.ext_lo(t) && c[q] < tl.ext_hi(t)) tlist[q][nt[q]++] = t;
-      }
+      if (q >= D) { tl[q][0] = 0; ll[q][0] = 0; nt[q] = 1; continue; }
+      const int4 e = __ldg(ra.axis_tab + c[q]);
+      tl[q][0] = e.x; ll[q][0] = e.y; tl[q][1] = e.z; ll[q][1] = e.w;
+      nt[q] = (restricted || e.z < 0) ? 1 : 2;
     }
     T s = 0;
     for (int iz = 0; iz < nt[2]; ++iz)
       for (int iy = 0; iy < nt[1]; ++iy)
         for (int ix = 0; ix < nt[0]; ++ix) {
-          const int tx = tlist[0][ix], ty = tlist[1][iy], tz = tlist[2][iz];
+          const int tx = tl[0][ix], ty = tl[1][iy], tz = tl[2][iz];
           const int pid = tx + ra.ntile * (ty + (D > 2 ? ra.ntile * tz : 0));
-          const int lx = c[0] - tl.ext_lo(tx), ly = c[1] - tl.ext_lo(ty);
-          const int Lx = tl.ext_hi(tx) - tl.ext_lo(tx), Ly = tl.ext_hi(ty) - tl.ext_lo(ty);
-          const int lz = D > 2 ? c[2] - tl.ext_lo(tz) : 0;
-          s += y[ra.yoff[pid] + lx + (long long)Lx * (ly + (long long)Ly * lz)];
+          const int Lx = __ldg(ra.axis_len + tx), Ly = __ldg(ra.axis_len + ty);
+          s += y[__ldg(ra.yoff + pid) + ll[0][ix] + (long long)Lx * (ll[1][iy] + (long long)Ly * ll[2][iz])];
         }
     const int mult = nt[0] * nt[1] * nt[2];
     z[a] += restricted ? s : s / (T)mult;
   }
 }
 
-// out[line, i] = sum_j S[i][j] in[line, j] along `axis`; optional divide by lam
-template <typename T, int D>
-__global__ void k_fdm_pass(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ S,
-                           const T* __restrict__ lam, int m, int axis, long long nn) {
-  long long stride = 1;
-  for (int k = 0; k < axis; ++k) stride *= m;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)((t / stride) % m);
-    const long long base = t - (long long)i * stride;
-    T acc = 0;
-    const T* Si = S + (size_t)i * m;
-    for (int j = 0; j < m; ++j) acc += Si[j] * in[base + (long long)j * stride];
-    out[t] = lam ? acc / lam[t] : acc;
+// Coarsest solve pass: out = S applied along one axis, as the GEMM
+// C[i][n] = sum_j S[i][j] B[j][n] with B[j][n] = in[(n / inner) m inner + j inner + n % inner]
+// (inner = m^axis), 32x32 output tiles, K chunks of 32 staged in shared
+// memory; optional division by the eigenvalues in the epilogue.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fdm_pass(const T* __restrict__ in, T* __restrict__ out,
+                                                   const T* __restrict__ S, const T* __restrict__ lam, int m,
+                                                   long long inner, long long ncols) {
+  __shared__ T sS[32][33];
+  __shared__ T sB[32][33];
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.y * 32;
+  const long long n0 = (long long)blockIdx.x * 32;
+  const int ti = tid >> 3, tn = (tid & 7) * 4;  // each thread: 1 row x 4 columns... (8 x 32 layout)
+  T acc[4] = {0, 0, 0, 0};
+  for (int j0 = 0; j0 < m; j0 += 32) {
+    __syncthreads();
+    for (int e = tid; e < 32 * 32; e += 256) {
+      const int r = e >> 5, cc = e & 31;
+      const int ii = i0 + r, jj = j0 + cc;
+      sS[r][cc] = (ii < m && jj < m) ? S[(size_t)ii * m + jj] : (T)0;
+      const int jb = j0 + r;
+      const long long nb = n0 + cc;
+      T v = 0;
+      if (jb < m && nb < ncols) v = in[(nb / inner) * m * inner + (long long)jb * inner + nb % inner];
+      sB[r][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const T sv = sS[ti][k];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += sv * sB[k][tn + q];
+    }
+  }
+  const int ii = i0 + ti;
+  if (ii >= m) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const long long nb = n0 + tn + q;
+    if (nb >= ncols) continue;
+    const long long o = (nb / inner) * m * inner + (long long)ii * inner + nb % inner;
+    out[o] = lam ? acc[q] / lam[o] : acc[q];
   }
 }
 
@@ -496,7 +556,9 @@ struct MGState {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t wexec = nullptr;
   bool fp32 = false;
+  long long graph_kernels = 0;  // kernel launches captured into the W-cycle graph
 };
+bool g_capturing = false;  // launches are being captured into the W-cycle graph
 std::map<const dcg_problem*, MGState> g_state;
 
 std::vector<int> level_sizes(int n, int max_levels) {
@@ -531,14 +593,25 @@ Stencil<double> q1_laplacian_over_d(int D, double h) {
   return st;
 }
 
+constexpr size_t kResidentSmem = 200 * 1024;
+
+template <typename T>
+bool ras_resident(int npmax) {
+  return sizeof(T) * ((size_t)npmax * npmax + (size_t)npmax * kNB) <= kResidentSmem;
+}
+template <typename T>
+long long ras_goff(int npmax) {
+  return ras_resident<T>(npmax) ? (long long)npmax * npmax : (long long)kKC * npmax;
+}
 template <typename T>
 size_t ras_smem_bytes(int npmax) {
-  return sizeof(T) * ((size_t)npmax * kNB + (size_t)kKC * npmax);
+  return sizeof(T) * ((size_t)ras_goff<T>(npmax) + (size_t)npmax * kNB);
 }
 
 void free_level(Level& L) {
   cudaFree(L.d_patch_class); cudaFree(L.d_patch_yoff); cudaFree(L.d_work); cudaFree(L.d_class_patches);
-  cudaFree(L.d_classes); cudaFree(L.d_inv); cudaFree(L.d_inv_bf16); cudaFree(L.f); cudaFree(L.z); cudaFree(L.y);
+  cudaFree(L.d_classes); cudaFree(L.d_origin); cudaFree(L.d_local); cudaFree(L.d_axis_tab); cudaFree(L.d_axis_len);
+  cudaFree(L.d_inv); cudaFree(L.d_inv_bf16); cudaFree(L.f); cudaFree(L.z); cudaFree(L.y);
   L = Level{};
 }
 
@@ -577,6 +650,8 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
     y += L.classes[c].np;
   }
   L.ylen = y < L.nn ? L.nn : y;
+  L.ras_np2 = 0;
+  for (int pid = 0; pid < L.npatch; ++pid) L.ras_np2 += (long long)L.classes[pclass[pid]].np * L.classes[pclass[pid]].np;
   L.nclass = (int)L.classes.size();
   L.npmax = 0;
   long long inv_total = 0;
@@ -604,6 +679,42 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
     }
   }
   L.nwork = (int)work.size() / 3;
+  // box origins, packed local coordinates per class, per-coordinate box table
+  std::vector<int4> origin(L.npatch);
+  for (int pid = 0; pid < L.npatch; ++pid) {
+    int t3[3] = {pid % nt, (pid / nt) % nt, D > 2 ? pid / (nt * nt) : 0};
+    int o3[3] = {0, 0, 0};
+    for (int k = 0; k < D; ++k) o3[k] = L.tiles.ext_lo(t3[k]);
+    long long node = o3[0] + (long long)L.m * o3[1] + (long long)L.m * L.m * o3[2];
+    origin[pid] = make_int4(o3[0], o3[1], o3[2], (int)node);
+  }
+  std::vector<int> local;
+  for (auto& c : L.classes) {
+    c.local_off = (int)local.size();
+    for (int k = 0; k < c.np; ++k) {
+      int lx = k % c.len[0], ly = (k / c.len[0]) % c.len[1], lz = k / (c.len[0] * c.len[1]);
+      local.push_back(lx | (ly << 10) | (lz << 20));
+    }
+  }
+  std::vector<int4> axis_tab(L.m);
+  for (int c = 0; c < L.m; ++c) {
+    const int t0 = c / o.patch;
+    int4 e = make_int4(t0, c - L.tiles.ext_lo(t0), -1, 0);
+    for (int t = t0 - 1; t <= t0 + 1; ++t) {
+      if (t == t0 || t < 0 || t >= nt) continue;
+      if (c >= L.tiles.ext_lo(t) && c < L.tiles.ext_hi(t)) { e.z = t; e.w = c - L.tiles.ext_lo(t); }
+    }
+    axis_tab[c] = e;
+  }
+  DCG_CUDA(cudaMalloc(&L.d_origin, sizeof(int4) * L.npatch));
+  DCG_CUDA(cudaMalloc(&L.d_local, sizeof(int) * local.size()));
+  DCG_CUDA(cudaMalloc(&L.d_axis_tab, sizeof(int4) * L.m));
+  DCG_CUDA(cudaMalloc(&L.d_axis_len, sizeof(int) * nt));
+  DCG_CUDA(cudaMemcpyAsync(L.d_origin, origin.data(), sizeof(int4) * L.npatch, cudaMemcpyHostToDevice, s));
+  DCG_CUDA(cudaMemcpyAsync(L.d_local, local.data(), sizeof(int) * local.size(), cudaMemcpyHostToDevice, s));
+  DCG_CUDA(cudaMemcpyAsync(L.d_axis_tab, axis_tab.data(), sizeof(int4) * L.m, cudaMemcpyHostToDevice, s));
+  DCG_CUDA(cudaMemcpyAsync(L.d_axis_len, len1.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s));
+  DCG_CUDA(cudaStreamSynchronize(s));
   DCG_CUDA(cudaMalloc(&L.d_patch_class, sizeof(int) * L.npatch));
   DCG_CUDA(cudaMalloc(&L.d_patch_yoff, sizeof(long long) * L.npatch));
   DCG_CUDA(cudaMalloc(&L.d_class_patches, sizeof(int) * grouped.size()));
@@ -662,41 +773,66 @@ template <typename T, int D>
 int coarse_solve_t(dcg_problem* p, const T* f, T* z, cudaStream_t s) {
   const Coarse& C = p->coarse;
   const long long nn = ipow(C.m, D);
+  const int prof = prof_begin(p, PC_COARSE, s, g_capturing);
   T* tmp = (T*)C.tmp;
   const T* S = coarse_S<T>(C);
   const T* lam = coarse_lam<T>(C);
-  const int g = grid_for(nn, 256, 4096);
+  const long long ncols = nn / C.m;
+  const dim3 grid((unsigned)((ncols + 31) / 32), (unsigned)((C.m + 31) / 32));
+  const long long in1 = 1, inm = C.m, inmm = (long long)C.m * C.m;
   if (D == 2) {
-    k_fdm_pass<T, D><<<g, 256, 0, s>>>(f, tmp, S, nullptr, C.m, 0, nn);
-    k_fdm_pass<T, D><<<g, 256, 0, s>>>(tmp, z, S, lam, C.m, 1, nn);
-    k_fdm_pass<T, D><<<g, 256, 0, s>>>(z, tmp, S, nullptr, C.m, 1, nn);
-    k_fdm_pass<T, D><<<g, 256, 0, s>>>(tmp, z, S, nullptr, C.m, 0, nn);
+    k_fdm_pass<T><<<grid, 256, 0, s>>>(f, tmp, S, nullptr, C.m, in1, ncols);
+    k_fdm_pass<T><<<grid, 256, 0, s>>>(tmp, z, S, lam, C.m, inm, ncols);
+    k_fdm_pass<T><<<grid, 256, 0, s>>>(z, tmp, S, nullptr, C.m, inm, ncols);
+    k_fdm_pass<T><<<grid, 256, 0, s>>>(tmp, z, S, nullptr, C.m, in1, ncols);
   } else {
-    k_fdm_pass<T, D><<<g, 256, 0, s>>>(f, tmp, S, nullptr, C.m, 0, nn);
-    k_fdm_pass<T, D><<<g, 256, 0, s>>>(tmp, z, S, nullptr, C.m, 1, nn);
-    k_fdm_pass<T, D><<<g, 256, 0, s>>>(z, tmp, S, lam, C.m, 2, nn);
-    k_fdm_pass<T, D><<<g, 256, 0, s>>>(tmp, z, S, nullptr, C.m, 2, nn);
-    k_fdm_pass<T, D><<<g, 256, 0, s>>>(z, tmp, S, nullptr, C.m, 1, nn);
-    k_fdm_pass<T, D><<<g, 256, 0, s>>>(tmp, z, S, nullptr, C.m, 0, nn);
+    k_fdm_pass<T><<<grid, 256, 0, s>>>(f, tmp, S, nullptr, C.m, in1, ncols);
+    k_fdm_pass<T><<<grid, 256, 0, s>>>(tmp, z, S, nullptr, C.m, inm, ncols);
+    k_fdm_pass<T><<<grid, 256, 0, s>>>(z, tmp, S, lam, C.m, inmm, ncols);
+    k_fdm_pass<T><<<grid, 256, 0, s>>>(tmp, z, S, nullptr, C.m, inmm, ncols);
+    k_fdm_pass<T><<<grid, 256, 0, s>>>(z, tmp, S, nullptr, C.m, inm, ncols);
+    k_fdm_pass<T><<<grid, 256, 0, s>>>(tmp, z, S, nullptr, C.m, in1, ncols);
   }
+  note_launches(2 * D - 1);  // the check below counts one
   DCG_LAUNCH_CHECK();
+  prof_end(p, prof, s, 2.0 * 2 * D * (double)nn * C.m,
+           sizeof(T) * (2.0 * 2 * D * (double)nn + (double)C.m * C.m + nn), g_capturing);
   return DCG_OK;
 }
 
 template <typename T, int D>
 int ras_step_t(dcg_problem* p, Level& L, cudaStream_t s) {
   RasArgs ra{};
-  ra.m = L.m; ra.ntile = L.tiles.ntile; ra.P = L.tiles.P; ra.o = L.tiles.o;
+  ra.m = L.m; ra.ntile = L.tiles.ntile;
   ra.work = L.d_work; ra.class_patches = L.d_class_patches; ra.classes = L.d_classes; ra.yoff = L.d_patch_yoff;
+  ra.origin = L.d_origin; ra.local = L.d_local; ra.axis_tab = L.d_axis_tab; ra.axis_len = L.d_axis_len;
   ra.nwork = L.nwork;
+  ra.g_off = ras_goff<T>(L.npmax);
   const size_t smem = ras_smem_bytes<T>(L.npmax);
-  int grid = std::min(L.nwork, 152 * 4);
-  k_ras_solve<T, D><<<grid, kRasThreads, smem, s>>>(ra, st_of<T>(L), (const T*)L.f, (const T*)L.z,
-                                                    (const T*)L.d_inv, (T*)L.y);
+  const bool resident = ras_resident<T>(L.npmax);
+  const int per_sm = std::max(1, (int)((227 * 1024) / (smem + 1024)));
+  const int cap = 152 * per_sm;
+  ra.items_per_cta = (L.nwork + cap - 1) / cap;
+  int grid = (L.nwork + ra.items_per_cta - 1) / ra.items_per_cta;
+  // algorithmic work: the shared-inverse products and the box data they touch
+  double flops = 0.0, bytes = 0.0;
+  for (const auto& c : L.classes) bytes += sizeof(T) * (double)c.np * c.np;
+  flops = 2.0 * (double)L.ras_np2;
+  bytes += sizeof(T) * 3.0 * (double)L.ylen;
+  int prof = prof_begin(p, PC_RAS_SOLVE, s, g_capturing);
+  if (resident)
+    k_ras_solve<T, D, true><<<grid, kRasThreads, smem, s>>>(ra, st_of<T>(L), (const T*)L.f, (const T*)L.z,
+                                                            (const T*)L.d_inv, (T*)L.y);
+  else
+    k_ras_solve<T, D, false><<<grid, kRasThreads, smem, s>>>(ra, st_of<T>(L), (const T*)L.f, (const T*)L.z,
+                                                             (const T*)L.d_inv, (T*)L.y);
   DCG_LAUNCH_CHECK();
+  prof_end(p, prof, s, flops, bytes, g_capturing);
+  prof = prof_begin(p, PC_RAS_UPDATE, s, g_capturing);
   k_ras_update<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(ra, (const T*)L.y, (T*)L.z, L.nn,
                                                                 p->opts.ras_weights == DCG_RAS_RESTRICTED);
   DCG_LAUNCH_CHECK();
+  prof_end(p, prof, s, (double)L.ylen, sizeof(T) * ((double)L.ylen + 2.0 * L.nn), g_capturing);
   return DCG_OK;
 }
 
@@ -706,16 +842,21 @@ int wcycle_t(dcg_problem* p, int k, cudaStream_t s) {
   if (k == 1) return coarse_solve_t<T, D>(p, (const T*)L.f, (T*)L.z, s);
   Level& Lc = p->levels[k - 2];
   for (int i = 0; i < p->opts.m1; ++i) DCG_TRY((ras_step_t<T, D>(p, L, s)));
+  int prof = prof_begin(p, PC_TRANSFER, s, g_capturing);
   k_residual<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(st_of<T>(L), (const T*)L.f, (const T*)L.z, (T*)L.y, L.m,
                                                              L.nn);
   DCG_LAUNCH_CHECK();
   k_restrict<T, D><<<grid_for(Lc.nn, 256, 8192), 256, 0, s>>>((const T*)L.y, (T*)Lc.f, L.m, Lc.m, Lc.nn);
   DCG_LAUNCH_CHECK();
+  prof_end(p, prof, s, 2.0 * (ipow(3, D) * (double)L.nn + ipow(3, D) * (double)Lc.nn),
+           sizeof(T) * (4.0 * L.nn + Lc.nn), g_capturing);
   DCG_CUDA(cudaMemsetAsync(Lc.z, 0, sizeof(T) * Lc.nn, s));
   DCG_TRY((wcycle_t<T, D>(p, k - 1, s)));
   DCG_TRY((wcycle_t<T, D>(p, k - 1, s)));
+  prof = prof_begin(p, PC_TRANSFER, s, g_capturing);
   k_prolong_add<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>((const T*)Lc.z, (T*)L.z, L.m, Lc.m, L.nn);
   DCG_LAUNCH_CHECK();
+  prof_end(p, prof, s, 2.0 * L.nn, sizeof(T) * (2.0 * L.nn + Lc.nn), g_capturing);
   for (int i = 0; i < p->opts.m2; ++i) DCG_TRY((ras_step_t<T, D>(p, L, s)));
   return DCG_OK;
 }
@@ -729,9 +870,15 @@ int wcycle_dispatch(dcg_problem* p, cudaStream_t s) {
 int build_wcycle_graph(dcg_problem* p) {
   MGState& S = g_state[p];
   if (S.wexec) { cudaGraphExecDestroy(S.wexec); S.wexec = nullptr; }
+  prof_clear_graph(p);
   if (!S.cap) DCG_CUDA(cudaStreamCreateWithFlags(&S.cap, cudaStreamNonBlocking));
   DCG_CUDA(cudaStreamBeginCapture(S.cap, cudaStreamCaptureModeThreadLocal));
+  g_capturing = true;
+  const long long before = g_launch_count;
   int st = S.fp32 ? wcycle_dispatch<float>(p, S.cap) : wcycle_dispatch<double>(p, S.cap);
+  S.graph_kernels = g_launch_count - before;
+  g_launch_count = before;
+  g_capturing = false;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(S.cap, &graph);
   if (st != DCG_OK) { if (graph) cudaGraphDestroy(graph); return st; }
@@ -746,6 +893,7 @@ int run_wcycle(dcg_problem* p, cudaStream_t s) {
   MGState& S = g_state[p];
   if (!S.wexec) DCG_TRY(build_wcycle_graph(p));
   DCG_CUDA(cudaGraphLaunch(S.wexec, s));
+  note_launches(S.graph_kernels);
   return DCG_OK;
 }
 
@@ -905,21 +1053,26 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
       DCG_LAUNCH_CHECK();
     }
   }
-  // RAS kernel shared memory opt-in
-  size_t smem_max = 0;
-  for (auto& L : p->levels) smem_max = std::max(smem_max, fp32 ? ras_smem_bytes<float>(L.npmax) : ras_smem_bytes<double>(L.npmax));
-  if (smem_max > 48 * 1024) {
-    if (fp32) {
-      DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-      DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-    } else {
-      DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-      DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-    }
+  // RAS kernel shared memory opt-in (largest configuration of each variant)
+  {
+    const int big = 227 * 1024;
+    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<float, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<float, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<float, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<float, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<double, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<double, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<double, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<double, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   }
   DCG_CUDA(cudaStreamSynchronize(s));
   if (!exact_mode(p)) DCG_TRY(build_wcycle_graph(p));
   return DCG_OK;
+}
+
+int mg_rebuild_graph(dcg_problem* p) {
+  if (p->levels.empty() || exact_mode(p)) return DCG_OK;
+  return build_wcycle_graph(p);
 }
 
 int mg_inner_apply(dcg_problem* p, const double* z, double* y, cudaStream_t s) {
@@ -939,11 +1092,13 @@ int inner_residual(dcg_problem* p, const double* g, const double* z, cudaStream_
   Level& L = p->levels.back();
   const int grid = grid_for(L.nn, 256, 4096);
   Reduce red = make_reduce(p, S_TMP0);  // S_TMP0 <- ||r||^2, S_TMP1 <- ||g||^2
+  const int prof = prof_begin(p, PC_INNER_RES, s);
   if (p->dim == 2)
     k_inner_residual<T, 2><<<grid, 256, 0, s>>>(L.st64, g, z, (T*)L.f, (T*)L.z, nullptr, L.m, L.nn, red);
   else
     k_inner_residual<T, 3><<<grid, 256, 0, s>>>(L.st64, g, z, (T*)L.f, (T*)L.z, nullptr, L.m, L.nn, red);
   DCG_LAUNCH_CHECK();
+  prof_end(p, prof, s, 2.0 * ipow(3, p->dim) * (double)L.nn, (16.0 + 2.0 * sizeof(T)) * L.nn);
   return DCG_OK;
 }
 
@@ -976,6 +1131,11 @@ int mg_cycles(dcg_problem* p, const double* g, double* z, int ncycles, cudaStrea
     DCG_TRY(fp32 ? inner_residual<float>(p, g, z, s) : inner_residual<double>(p, g, z, s));
     DCG_TRY(run_wcycle(p, s));
     DCG_TRY(fp32 ? accumulate<float>(p, z, s) : accumulate<double>(p, z, s));
+    if (p->prof.mask) {
+      DCG_CUDA(cudaStreamSynchronize(s));
+      prof_flush_graph(p);
+      prof_flush(p);
+    }
   }
   return DCG_OK;
 }
@@ -989,6 +1149,7 @@ int mg_solve(dcg_problem* p, const double* g, double* z, double tol, int nmax, i
   for (;;) {
     DCG_TRY(fp32 ? inner_residual<float>(p, g, z, s) : inner_residual<double>(p, g, z, s));
     DCG_TRY(read_scalars(p, s));
+    if (n > 0 && p->prof.mask) prof_flush_graph(p);  // the replay before this read
     const double rn = std::sqrt(p->scal_host[S_TMP0]);
     const double gn = std::sqrt(p->scal_host[S_TMP1]);
     if (!(gn > 0.0)) break;

@@ -197,9 +197,11 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged) 
       DCG_CUDA(cudaMemcpyAsync(b.coef + b.ndir_cap + slot, p->scal + S_DQ, sizeof(double), cudaMemcpyDeviceToDevice, s));
       ++ndir;
     }
+    int prof = prof_begin(p, PC_VEC, s);
     k_update<<<grid_n(N), kRedThreads, 0, s>>>(b.xh, b.r, b.d, b.q, N, p->scal, c.rule != R_FR,
                                                make_reduce(p, S_RRN));
     DCG_LAUNCH_CHECK();
+    prof_end(p, prof, s, 8.0 * N, 48.0 * N);
     c.st->outer_its++;
     DCG_TRY(read_scalars(p, s));
     const double dq = p->scal_host[S_DQ];
@@ -224,8 +226,10 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged) 
                                                           make_reduce(p, S_DR));
       DCG_LAUNCH_CHECK();
     } else {
+      prof = prof_begin(p, PC_VEC, s);
       k_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, N, p->scal, c.rule == R_FCG1, make_reduce(p, S_DR));
       DCG_LAUNCH_CHECK();
+      prof_end(p, prof, s, 4.0 * N, 24.0 * N);
     }
     k_roll<<<1, 1, 0, s>>>(p->scal);
     DCG_LAUNCH_CHECK();
@@ -253,8 +257,10 @@ int plain_cg(Ctx& c, const double* f, double* x) {
   bool conv = std::sqrt(rr) <= c.eps;
   while (!conv && c.st->outer_its < c.max_it) {
     DCG_TRY(spmv_dot(p, b.d, b.q, b.d, S_DQ, s));
+    int prof = prof_begin(p, PC_VEC, s);
     k_update<<<grid_n(N), kRedThreads, 0, s>>>(x, b.r, b.d, b.q, N, p->scal, 0, make_reduce(p, S_RRN));
     DCG_LAUNCH_CHECK();
+    prof_end(p, prof, s, 8.0 * N, 48.0 * N);
     c.st->outer_its++;
     bool check = (c.st->outer_its % std::max(1, p->opts.check_every)) == 0;
     if (check) {
@@ -270,8 +276,10 @@ int plain_cg(Ctx& c, const double* f, double* x) {
         break;
       }
     }
+    prof = prof_begin(p, PC_VEC, s);
     k_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, N, p->scal, 0, make_reduce(p, S_DR));
     DCG_LAUNCH_CHECK();
+    prof_end(p, prof, s, 4.0 * N, 24.0 * N);
     k_roll<<<1, 1, 0, s>>>(p->scal);
     DCG_LAUNCH_CHECK();
   }
@@ -283,6 +291,7 @@ int plain_cg(Ctx& c, const double* f, double* x) {
 int read_scalars(dcg_problem* p, cudaStream_t s) {
   DCG_CUDA(cudaMemcpyAsync(p->scal_host, p->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
   DCG_CUDA(cudaStreamSynchronize(s));
+  if (p->prof.mask) prof_flush(p);
   return DCG_OK;
 }
 

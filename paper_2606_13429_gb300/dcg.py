@@ -30,6 +30,7 @@ DCG_FCG1, DCG_FR, DCG_FCG_INF = 0, 1, 2
 DCG_FP64, DCG_MIXED = 0, 1
 DCG_INV_FP32, DCG_INV_BF16 = 0, 1
 DCG_RAS_MULTIPLICITY, DCG_RAS_RESTRICTED = 0, 1
+PROF_CLASSES = ["spmv", "vec", "ras_solve", "ras_update", "transfer", "coarse", "inner_res"]
 
 
 class dcg_mesh(C.Structure):
@@ -92,6 +93,9 @@ def load(path: str = LIB_PATH):
         "dcg_mg_solve": (I, [P, VP, VP, D, I, C.POINTER(I), VP]),
         "dcg_ras_step": (I, [P, I, VP, VP, VP]),
         "dcg_coarse_solve": (I, [P, VP, VP, VP]),
+        "dcg_profile_enable": (I, [P, C.c_uint, VP]),
+        "dcg_profile_read": (I, [P, I, C.POINTER(D), C.POINTER(LL), C.POINTER(D), C.POINTER(D), VP]),
+        "dcg_kernel_launches": (LL, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -305,3 +309,25 @@ def dcg_ras_step(prob: Problem, level, f, z, stream=None):
 def dcg_coarse_solve(prob: Problem, f, z, stream=None):
     _check(load().dcg_coarse_solve(prob.ptr, _dptr(f, name="f"), _dptr(z, name="z"), _stream(stream)),
            "dcg_coarse_solve")
+
+
+def dcg_profile_enable(prob: Problem, classes=(), stream=None):
+    """Time the named kernel classes (see PROF_CLASSES) with CUDA events."""
+    mask = 0
+    for c in classes:
+        mask |= 1 << PROF_CLASSES.index(c)
+    _check(load().dcg_profile_enable(prob.ptr, mask, _stream(stream)), "dcg_profile_enable")
+
+
+def dcg_profile_read(prob: Problem, stream=None) -> dict:
+    out = {}
+    for i, name in enumerate(PROF_CLASSES):
+        ms, n, fl, by = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
+        _check(load().dcg_profile_read(prob.ptr, i, C.byref(ms), C.byref(n), C.byref(fl), C.byref(by),
+                                       _stream(stream)), "dcg_profile_read")
+        out[name] = {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
+    return out
+
+
+def dcg_kernel_launches() -> int:
+    return int(load().dcg_kernel_launches())
