@@ -150,14 +150,13 @@ struct Level {
   int npatch = 0, nclass = 0, npmax = 0;
   std::vector<RasClass> classes;
   int* d_patch_class = nullptr;     // [npatch]
-  long long* d_patch_yoff = nullptr;  // [npatch]
   int* d_work = nullptr;            // [nwork * 3] (class, first index into d_class_patches, count)
   int* d_class_patches = nullptr;   // patch ids grouped by class
   RasClass* d_classes = nullptr;
   int4* d_origin = nullptr;         // [npatch] box origin coordinates and node
   int* d_local = nullptr;           // packed local coordinates of every class
   int4* d_axis_tab = nullptr;       // [m] boxes containing each coordinate
-  int* d_axis_len = nullptr;        // [ntile] box extent per tile
+  int2* d_core = nullptr;           // [npatch] core tile in box-local coordinates
   int nwork = 0;
   long long ylen = 0;
   long long ras_np2 = 0;            // sum over boxes of np^2 (FMAs of one smoothing product)
@@ -166,7 +165,7 @@ struct Level {
   // vectors in the W-cycle precision
   void* f = nullptr;
   void* z = nullptr;
-  void* y = nullptr;                // RAS patch results
+  void* y = nullptr;                // RAS box results, node-major (2^d slots per node)
 };
 
 struct Coarse {
@@ -244,7 +243,7 @@ namespace dcg {
 // Pairs written by one two-value reduction are consecutive:
 // (S_RRN, S_RQ) by the CG update, (S_TMP0, S_TMP1) by the inner residual.
 enum Scal {
-  S_DQ = 0, S_DR, S_RR, S_RRN, S_RQ, S_GG, S_FF, S_TMP0, S_TMP1, S_ALPHA, S_BETA, S_RES,
+  S_DQ = 0, S_DR, S_RR, S_RRN, S_RQ, S_GG, S_FF, S_TMP0, S_TMP1, S_ALPHA, S_BETA, S_RES, S_ERR,
   S_COUNT = 16
 };
 constexpr int kNumCounters = 8;

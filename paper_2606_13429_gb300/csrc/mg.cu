@@ -31,6 +31,7 @@
 // each cycle as a correction: z <- z + W(g - Z_J z, 0), which equals
 // W(g, z) for the affine W-cycle iteration.
 #include "common.cuh"
+#include "tma.cuh"
 
 #include <cmath>
 #include <cstdio>
@@ -41,7 +42,8 @@ namespace {
 
 constexpr int kNB = 32;       // boxes per CTA batch in the RAS GEMM
 constexpr int kKC = 32;       // K chunk of the inverse staged in shared memory
-constexpr int kRasThreads = 256;
+constexpr int kRasThreads = 1024;  // 32 warps per work item: latency hiding on sparse levels
+constexpr int kRowGroups = kRasThreads / 8;  // row groups of the GEMM (8 groups of 4 boxes)
 constexpr int kMaxNp = 256;   // largest box (nodes) supported
 
 // ---------------------------------------------------------------------------
@@ -226,9 +228,19 @@ __global__ void k_to_t(const double* __restrict__ a, T* __restrict__ b, long lon
 
 template <int D>
 __device__ __forceinline__ void coords_of(long long a, int m, int (&c)[3]) {
-  c[0] = (int)(a % m);
-  c[1] = (int)((a / m) % m);
-  c[2] = D > 2 ? (int)(a / ((long long)m * m)) : 0;
+  // node counts stay below 2^31: 32-bit unsigned division (64-bit division
+  // is emulated and costs about a hundred instructions)
+  const unsigned ua = (unsigned)a, um = (unsigned)m;
+  const unsigned q = ua / um;
+  c[0] = (int)(ua - q * um);
+  if (D > 2) {
+    const unsigned q2 = q / um;
+    c[1] = (int)(q - q2 * um);
+    c[2] = (int)q2;
+  } else {
+    c[1] = (int)q;
+    c[2] = 0;
+  }
 }
 
 template <typename T, int D>
@@ -248,7 +260,7 @@ __device__ __forceinline__ T stencil_apply(const Stencil<T>& st, const T* __rest
         const int xc = c[0] + dx;
         if (xc < 0 || xc >= m) continue;
         const T w = st.c[(dx + 1) + 3 * (dy + 1) + (D > 2 ? 9 * (dz + 1) : 0)];
-        acc += w * z[xc + (long long)m * yc + (D > 2 ? mm * zc : 0)];
+        acc += w * __ldg(z + xc + (long long)m * yc + (D > 2 ? mm * zc : 0));
       }
     }
   }
@@ -324,31 +336,46 @@ struct RasArgs {
   const int* work;           // [nwork*3]: class, first index into class_patches, count
   const int* class_patches;  // patch ids grouped by class
   const RasClass* classes;
-  const long long* yoff;     // [npatch] offset of the box's results in y
   const int4* origin;        // [npatch] box origin (x, y, z) and its node index
+  const int2* core;          // [npatch] core tile in box-local coordinates, packed 10 bits per axis (lo, hi)
   const int* local;          // per class: packed local coordinates, 10 bits per axis
-  const int4* axis_tab;      // [m] per coordinate: (t0, l0, t1, l1) boxes containing it, -1 = none
-  const int* axis_len;       // [ntile] box extent per tile along an axis
-  int ntile;
+  const int4* axis_tab;      // [m] per coordinate: (t0, l0, t1, l1), t1 = -1 when one box only
   int nwork;
   int items_per_cta;
   long long g_off;           // elements of shared memory before the residual tile
+  double* err;               // device error slot (set to 1 when a bounded wait gives up)
 };
 
+// Box results are stored node-major: y[node * SL + slot], SL = 2^D, where bit
+// `ax` of `slot` says whether the box is the node's own core tile along axis
+// ax (0) or the neighbouring tile whose overlap reaches the node (1); with
+// 2*overlap <= patch a node lies in at most two boxes per axis.
+template <int D>
+constexpr int slots_per_node() { return 1 << D; }
+
 // (1) residual on each box of a batch, times the shared inverse, to y.
-// A CTA walks a contiguous range of work items (sorted by class) and keeps
-// the class inverse in shared memory while the class does not change.
+// A CTA walks a contiguous range of work items (sorted by class); when
+// RESIDENT, the class inverse is brought into shared memory with one bulk
+// asynchronous copy while the residuals are gathered, and kept while the
+// class does not change.
 template <typename T, int D, bool RESIDENT>
 __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, Stencil<T> st, const T* __restrict__ f,
                                                             const T* __restrict__ z, const T* __restrict__ inv,
                                                             T* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
   const int tid = threadIdx.x;
   const int tx = tid & 7;   // group of 4 boxes
-  const int ty = tid >> 3;  // rows ty, ty+32, ...
+  const int ty = tid >> 3;  // rows ty, ty+kRowGroups, ...
   const int w0 = blockIdx.x * ra.items_per_cta;
   const int w1 = min(ra.nwork, w0 + ra.items_per_cta);
+  if (RESIDENT) {
+    if (tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+  }
+  unsigned phase = 0;
   int cur_cls = -1;
+  constexpr int SL = slots_per_node<D>();
   for (int w = w0; w < w1; ++w) {
     const int cls = ra.work[3 * w], first = ra.work[3 * w + 1], nb = ra.work[3 * w + 2];
     const RasClass C = ra.classes[cls];
@@ -356,41 +383,61 @@ __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, Stencil<T
     T* As = reinterpret_cast<T*>(smem_raw);                 // RESIDENT: [np][np], else [kKC][np]
     T* G = As + ra.g_off;                                   // [np][kNB]
     __syncthreads();
+    bool loading = false;
     if (RESIDENT && cls != cur_cls) {
-      const T* src = inv + C.inv_off;
-      for (int idx = tid; idx < np * np; idx += blockDim.x) As[idx] = src[idx];
+      if (tid == 0) {
+        const unsigned bytes = (unsigned)((((size_t)np * np * sizeof(T)) + 15) & ~(size_t)15);
+        mbar_expect_tx(&bar, bytes);
+        tma_load_1d(As, inv + C.inv_off, bytes, &bar);
+      }
+      loading = true;
       cur_cls = cls;
     }
-    // gather residuals f - Z z on the boxes (box index fastest)
-    for (int idx = tid; idx < np * kNB; idx += blockDim.x) {
-      const int b = idx % kNB, k = idx / kNB;
-      T r = 0;
-      if (b < nb) {
-        const int pid = ra.class_patches[first + b];
-        const int4 o4 = ra.origin[pid];
-        const int pk = ra.local[C.local_off + k];
-        int c[3] = {o4.x + (pk & 1023), o4.y + ((pk >> 10) & 1023), o4.z + ((pk >> 20) & 1023)};
-        const long long a = (long long)o4.w + (pk & 1023) + (long long)ra.m * (((pk >> 10) & 1023) +
-                            (D > 2 ? (long long)ra.m * ((pk >> 20) & 1023) : 0));
-        r = f[a] - stencil_apply<T, D>(st, z, ra.m, c);
+    // gather residuals f - Z z on the boxes: thread keeps box b = tid % kNB
+    // and walks local nodes k = tid / kNB + j * (threads / kNB)
+    {
+      const int b = tid % kNB;
+      const int kstep = blockDim.x / kNB;
+      int4 o4 = make_int4(0, 0, 0, 0);
+      if (b < nb) o4 = __ldg(ra.origin + __ldg(ra.class_patches + first + b));
+#pragma unroll 6
+      for (int k = tid / kNB; k < np; k += kstep) {
+        T r = 0;
+        if (b < nb) {
+          const int pk = __ldg(ra.local + C.local_off + k);
+          const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = (pk >> 20) & 1023;
+          int c[3] = {o4.x + lx, o4.y + ly, o4.z + lz};
+          const long long a = (long long)o4.w + lx + (long long)ra.m * (ly + (D > 2 ? (long long)ra.m * lz : 0));
+          r = __ldg(f + a) - stencil_apply<T, D>(st, z, ra.m, c);
+        }
+        G[(size_t)k * kNB + b] = r;
       }
-      G[(size_t)k * kNB + b] = r;
     }
-    constexpr int RI = kMaxNp / 32;
+    bool ok = true;
+    if (loading) {
+      // every thread waits (bounded) for the bulk copy it is about to read;
+      // a second bounded wait lets a slow copy in flight finish
+      ok = mbar_wait_bounded(&bar, phase) || mbar_wait_bounded(&bar, phase);
+      phase ^= 1u;
+    }
+    constexpr int RI = (kMaxNp + kRowGroups - 1) / kRowGroups;
     T acc[RI][4];
 #pragma unroll
     for (int r = 0; r < RI; ++r)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[r][c] = 0;
     if (RESIDENT) {
-      __syncthreads();
+      if (__syncthreads_or(!ok)) {  // uniform decision after the barrier
+        if (tid == 0) *ra.err = 1.0;
+        return;
+      }
       for (int kk = 0; kk < np; ++kk) {
         const T* g = G + (size_t)kk * kNB + 4 * tx;
         const T g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3];
         const T* arow = As + (size_t)kk * np;
 #pragma unroll
         for (int r = 0; r < RI; ++r) {
-          const int i = ty + 32 * r;
+          const int i = ty + kRowGroups * r;
           if (i < np) {
             const T av = arow[i];
             acc[r][0] += av * g0;
@@ -405,7 +452,8 @@ __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, Stencil<T
       for (int k0 = 0; k0 < np; k0 += kKC) {
         const int kc = min(kKC, np - k0);
         __syncthreads();
-        for (int idx = tid; idx < kc * np; idx += blockDim.x) As[idx] = invc[(size_t)k0 * np + idx];
+#pragma unroll 8
+        for (int idx = tid; idx < kc * np; idx += blockDim.x) As[idx] = __ldg(invc + (size_t)k0 * np + idx);
         __syncthreads();
         for (int kk = 0; kk < kc; ++kk) {
           const T* g = G + (size_t)(k0 + kk) * kNB + 4 * tx;
@@ -413,7 +461,7 @@ __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, Stencil<T
           const T* arow = As + (size_t)kk * np;
 #pragma unroll
           for (int r = 0; r < RI; ++r) {
-            const int i = ty + 32 * r;
+            const int i = ty + kRowGroups * r;
             if (i < np) {
               const T av = arow[i];
               acc[r][0] += av * g0;
@@ -425,92 +473,134 @@ __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, Stencil<T
         }
       }
     }
+    // epilogue: node-major results with the box's slot per node
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int b = 4 * tx + c;
       if (b >= nb) continue;
-      const int pid = ra.class_patches[first + b];
-      T* yp = y + ra.yoff[pid];
+      const int pid = __ldg(ra.class_patches + first + b);
+      const int4 o4 = __ldg(ra.origin + pid);
+      const int2 cb = __ldg(ra.core + pid);
 #pragma unroll
       for (int r = 0; r < RI; ++r) {
-        const int i = ty + 32 * r;
-        if (i < np) yp[i] = acc[r][c];
+        const int i = ty + kRowGroups * r;
+        if (i < np) {
+          const int pk = __ldg(ra.local + C.local_off + i);
+          const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = (pk >> 20) & 1023;
+          int slot = (lx < (cb.x & 1023) || lx >= (cb.y & 1023)) ? 1 : 0;
+          slot |= (ly < ((cb.x >> 10) & 1023) || ly >= ((cb.y >> 10) & 1023)) ? 2 : 0;
+          if (D > 2) slot |= (lz < ((cb.x >> 20) & 1023) || lz >= ((cb.y >> 20) & 1023)) ? 4 : 0;
+          const long long a = (long long)o4.w + lx + (long long)ra.m * (ly + (D > 2 ? (long long)ra.m * lz : 0));
+          y[a * SL + slot] = acc[r][c];
+        }
       }
     }
   }
 }
 
-// (2) z[j] += D_j * sum over boxes containing j of y_box[local(j)], with the
-// boxes found from per-coordinate tables (no integer division).
+// (2) z[j] += D_j * sum of the box results stored for node j (node-major
+// slots; which slots exist comes from the per-coordinate table).
 template <typename T, int D>
 __global__ void k_ras_update(RasArgs ra, const T* __restrict__ y, T* __restrict__ z, long long nn, int restricted) {
+  constexpr int SL = slots_per_node<D>();
   for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nn; a += (long long)gridDim.x * blockDim.x) {
     int c[3];
     coords_of<D>(a, ra.m, c);
-    int tl[3][2], ll[3][2], nt[3];
+    T v[SL];
+    if (sizeof(T) == 4 && SL >= 4) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if (q >= D) { tl[q][0] = 0; ll[q][0] = 0; nt[q] = 1; continue; }
-      const int4 e = __ldg(ra.axis_tab + c[q]);
-      tl[q][0] = e.x; ll[q][0] = e.y; tl[q][1] = e.z; ll[q][1] = e.w;
-      nt[q] = (restricted || e.z < 0) ? 1 : 2;
+      for (int q = 0; q < SL; q += 4) {
+        const float4 t4 = __ldg(reinterpret_cast<const float4*>(y + a * SL + q));
+        v[q] = t4.x; v[q + 1] = t4.y; v[q + 2] = t4.z; v[q + 3] = t4.w;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < SL; q += 2) {
+        const double2 t2 = __ldg(reinterpret_cast<const double2*>(y + a * SL + q));
+        v[q] = (T)t2.x; v[q + 1] = (T)t2.y;
+      }
     }
-    T s = 0;
-    for (int iz = 0; iz < nt[2]; ++iz)
-      for (int iy = 0; iy < nt[1]; ++iy)
-        for (int ix = 0; ix < nt[0]; ++ix) {
-          const int tx = tl[0][ix], ty = tl[1][iy], tz = tl[2][iz];
-          const int pid = tx + ra.ntile * (ty + (D > 2 ? ra.ntile * tz : 0));
-          const int Lx = __ldg(ra.axis_len + tx), Ly = __ldg(ra.axis_len + ty);
-          s += y[__ldg(ra.yoff + pid) + ll[0][ix] + (long long)Lx * (ll[1][iy] + (long long)Ly * ll[2][iz])];
-        }
-    const int mult = nt[0] * nt[1] * nt[2];
+    T s = v[0];
+    int mult = 1;
+    if (!restricted) {
+      int other[3] = {0, 0, 0};
+#pragma unroll
+      for (int q = 0; q < D; ++q) other[q] = __ldg(&ra.axis_tab[c[q]].z) >= 0;
+#pragma unroll
+      for (int sl = 1; sl < SL; ++sl) {
+        bool ok = true;
+#pragma unroll
+        for (int q = 0; q < D; ++q)
+          if ((sl >> q) & 1) ok = ok && other[q];
+        if (ok) s += v[sl];
+      }
+      mult = (1 + other[0]) * (1 + other[1]) * (D > 2 ? (1 + other[2]) : 1);
+    }
     z[a] += restricted ? s : s / (T)mult;
   }
 }
 
 // Coarsest solve pass: out = S applied along one axis, as the GEMM
 // C[i][n] = sum_j S[i][j] B[j][n] with B[j][n] = in[(n / inner) m inner + j inner + n % inner]
-// (inner = m^axis), 32x32 output tiles, K chunks of 32 staged in shared
-// memory; optional division by the eigenvalues in the epilogue.
-template <typename T>
+// (inner = m^axis). A CTA owns a 32x32 tile of C; the whole 32 x m panel of
+// S and m x 32 panel of B are staged in shared memory in one load round
+// (for axis 0, B's columns are contiguous in memory and the panel is stored
+// transposed), then 256 threads compute 4 outputs each; optional division by
+// the eigenvalues in the epilogue.
+template <typename T, bool AXIS0>
 __global__ void __launch_bounds__(256) k_fdm_pass(const T* __restrict__ in, T* __restrict__ out,
                                                    const T* __restrict__ S, const T* __restrict__ lam, int m,
                                                    long long inner, long long ncols) {
-  __shared__ T sS[32][33];
-  __shared__ T sB[32][33];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int mp = m + 1;                                   // padded row length
+  T* sS = reinterpret_cast<T*>(smem_raw);                 // [32][mp]
+  T* sB = sS + 32 * mp;                                   // AXIS0: [32][mp] (n-major), else [m][32]
   const int tid = threadIdx.x;
   const int i0 = blockIdx.y * 32;
-  const long long n0 = (long long)blockIdx.x * 32;
-  const int ti = tid >> 3, tn = (tid & 7) * 4;  // each thread: 1 row x 4 columns... (8 x 32 layout)
-  T acc[4] = {0, 0, 0, 0};
-  for (int j0 = 0; j0 < m; j0 += 32) {
-    __syncthreads();
-    for (int e = tid; e < 32 * 32; e += 256) {
-      const int r = e >> 5, cc = e & 31;
-      const int ii = i0 + r, jj = j0 + cc;
-      sS[r][cc] = (ii < m && jj < m) ? S[(size_t)ii * m + jj] : (T)0;
-      const int jb = j0 + r;
-      const long long nb = n0 + cc;
+  const unsigned n0 = blockIdx.x * 32u;
+  const unsigned ui = (unsigned)inner;
+  // one load round: S rows i0..i0+31, B columns n0..n0+31
+#pragma unroll 4
+  for (int e = tid; e < 32 * m; e += 256) {
+    const int r = e / m, j = e - r * m;
+    const int ii = i0 + r;
+    sS[r * mp + j] = ii < m ? __ldg(S + (size_t)ii * m + j) : (T)0;
+    if (AXIS0) {
+      const unsigned nb = n0 + r;  // column r of the panel, element j
+      sB[r * mp + j] = nb < (unsigned)ncols ? __ldg(in + (size_t)nb * m + j) : (T)0;
+    }
+  }
+  if (!AXIS0) {
+#pragma unroll 4
+    for (int e = tid; e < 32 * m; e += 256) {
+      const int j = e >> 5, c = e & 31;
+      const unsigned nb = n0 + c;
       T v = 0;
-      if (jb < m && nb < ncols) v = in[(nb / inner) * m * inner + (long long)jb * inner + nb % inner];
-      sB[r][cc] = v;
+      if (nb < (unsigned)ncols) {
+        const unsigned hi = nb / ui;
+        v = __ldg(in + (size_t)hi * m * ui + (size_t)j * ui + (nb - hi * ui));
+      }
+      sB[j * 32 + c] = v;
     }
-    __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < 32; ++k) {
-      const T sv = sS[ti][k];
+  }
+  __syncthreads();
+  const int ti = tid >> 3, tn = (tid & 7) * 4;
+  T acc[4] = {0, 0, 0, 0};
+  const T* srow = sS + ti * mp;
+#pragma unroll 4
+  for (int k = 0; k < m; ++k) {
+    const T sv = srow[k];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += sv * sB[k][tn + q];
-    }
+    for (int q = 0; q < 4; ++q) acc[q] += sv * (AXIS0 ? sB[(tn + q) * mp + k] : sB[k * 32 + tn + q]);
   }
   const int ii = i0 + ti;
   if (ii >= m) return;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const long long nb = n0 + tn + q;
-    if (nb >= ncols) continue;
-    const long long o = (nb / inner) * m * inner + (long long)ii * inner + nb % inner;
+    const unsigned nb = n0 + tn + q;
+    if (nb >= (unsigned)ncols) continue;
+    const unsigned hi = nb / ui;
+    const long long o = (long long)hi * m * ui + (long long)ii * ui + (nb - hi * ui);
     out[o] = lam ? acc[q] / lam[o] : acc[q];
   }
 }
@@ -593,7 +683,16 @@ Stencil<double> q1_laplacian_over_d(int D, double h) {
   return st;
 }
 
-constexpr size_t kResidentSmem = 200 * 1024;
+constexpr size_t kResidentSmem = 220 * 1024;  // dynamic shared memory of a resident-inverse CTA
+
+template <typename K>
+int set_ras_smem(K kernel) {
+  cudaFuncAttributes fa{};
+  DCG_CUDA(cudaFuncGetAttributes(&fa, kernel));
+  const int cap = 227 * 1024 - (int)fa.sharedSizeBytes;
+  DCG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  return DCG_OK;
+}
 
 template <typename T>
 bool ras_resident(int npmax) {
@@ -601,7 +700,8 @@ bool ras_resident(int npmax) {
 }
 template <typename T>
 long long ras_goff(int npmax) {
-  return ras_resident<T>(npmax) ? (long long)npmax * npmax : (long long)kKC * npmax;
+  // the bulk copy moves whole 16-byte chunks: round the inverse region up
+  return ras_resident<T>(npmax) ? ((long long)npmax * npmax + 3) / 4 * 4 : (long long)kKC * npmax;
 }
 template <typename T>
 size_t ras_smem_bytes(int npmax) {
@@ -609,8 +709,8 @@ size_t ras_smem_bytes(int npmax) {
 }
 
 void free_level(Level& L) {
-  cudaFree(L.d_patch_class); cudaFree(L.d_patch_yoff); cudaFree(L.d_work); cudaFree(L.d_class_patches);
-  cudaFree(L.d_classes); cudaFree(L.d_origin); cudaFree(L.d_local); cudaFree(L.d_axis_tab); cudaFree(L.d_axis_len);
+  cudaFree(L.d_patch_class); cudaFree(L.d_work); cudaFree(L.d_class_patches);
+  cudaFree(L.d_classes); cudaFree(L.d_origin); cudaFree(L.d_core); cudaFree(L.d_local); cudaFree(L.d_axis_tab);
   cudaFree(L.d_inv); cudaFree(L.d_inv_bf16); cudaFree(L.f); cudaFree(L.z); cudaFree(L.y);
   L = Level{};
 }
@@ -626,8 +726,6 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
   for (int t = 0; t < nt; ++t) len1[t] = L.tiles.ext_hi(t) - L.tiles.ext_lo(t);
   std::map<std::vector<int>, int> cls_of;
   std::vector<int> pclass(L.npatch);
-  std::vector<long long> yoff(L.npatch);
-  long long y = 0;
   L.classes.clear();
   for (int pid = 0; pid < L.npatch; ++pid) {
     int t3[3] = {pid % nt, (pid / nt) % nt, D > 2 ? pid / (nt * nt) : 0};
@@ -646,10 +744,8 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
       c = it->second;
     }
     pclass[pid] = c;
-    yoff[pid] = y;
-    y += L.classes[c].np;
   }
-  L.ylen = y < L.nn ? L.nn : y;
+  L.ylen = L.nn * (1LL << D);  // node-major results, 2^D slots per node
   L.ras_np2 = 0;
   for (int pid = 0; pid < L.npatch; ++pid) L.ras_np2 += (long long)L.classes[pclass[pid]].np * L.classes[pclass[pid]].np;
   L.nclass = (int)L.classes.size();
@@ -660,8 +756,8 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
       set_error_msg("RAS box larger than 256 nodes: reduce patch/overlap");
       return DCG_ERR_UNSUPPORTED;
     }
-    c.inv_off = inv_total;
-    inv_total += (long long)c.np * c.np;
+    c.inv_off = inv_total;  // 16-byte aligned for the bulk copy into shared memory
+    inv_total += ((long long)c.np * c.np + 3) / 4 * 4;
     L.npmax = std::max(L.npmax, c.np);
   }
   // group patches by class, batch into work items
@@ -681,12 +777,19 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
   L.nwork = (int)work.size() / 3;
   // box origins, packed local coordinates per class, per-coordinate box table
   std::vector<int4> origin(L.npatch);
+  std::vector<int2> core(L.npatch);
   for (int pid = 0; pid < L.npatch; ++pid) {
     int t3[3] = {pid % nt, (pid / nt) % nt, D > 2 ? pid / (nt * nt) : 0};
     int o3[3] = {0, 0, 0};
-    for (int k = 0; k < D; ++k) o3[k] = L.tiles.ext_lo(t3[k]);
+    int lo = 0, hi = 0;
+    for (int k = 0; k < D; ++k) {
+      o3[k] = L.tiles.ext_lo(t3[k]);
+      lo |= (L.tiles.core_lo(t3[k]) - o3[k]) << (10 * k);
+      hi |= (L.tiles.core_hi(t3[k]) - o3[k]) << (10 * k);
+    }
     long long node = o3[0] + (long long)L.m * o3[1] + (long long)L.m * L.m * o3[2];
     origin[pid] = make_int4(o3[0], o3[1], o3[2], (int)node);
+    core[pid] = make_int2(lo, hi);
   }
   std::vector<int> local;
   for (auto& c : L.classes) {
@@ -709,19 +812,17 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
   DCG_CUDA(cudaMalloc(&L.d_origin, sizeof(int4) * L.npatch));
   DCG_CUDA(cudaMalloc(&L.d_local, sizeof(int) * local.size()));
   DCG_CUDA(cudaMalloc(&L.d_axis_tab, sizeof(int4) * L.m));
-  DCG_CUDA(cudaMalloc(&L.d_axis_len, sizeof(int) * nt));
+  DCG_CUDA(cudaMalloc(&L.d_core, sizeof(int2) * L.npatch));
+  DCG_CUDA(cudaMemcpyAsync(L.d_core, core.data(), sizeof(int2) * L.npatch, cudaMemcpyHostToDevice, s));
   DCG_CUDA(cudaMemcpyAsync(L.d_origin, origin.data(), sizeof(int4) * L.npatch, cudaMemcpyHostToDevice, s));
   DCG_CUDA(cudaMemcpyAsync(L.d_local, local.data(), sizeof(int) * local.size(), cudaMemcpyHostToDevice, s));
   DCG_CUDA(cudaMemcpyAsync(L.d_axis_tab, axis_tab.data(), sizeof(int4) * L.m, cudaMemcpyHostToDevice, s));
-  DCG_CUDA(cudaMemcpyAsync(L.d_axis_len, len1.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, s));
   DCG_CUDA(cudaStreamSynchronize(s));
   DCG_CUDA(cudaMalloc(&L.d_patch_class, sizeof(int) * L.npatch));
-  DCG_CUDA(cudaMalloc(&L.d_patch_yoff, sizeof(long long) * L.npatch));
   DCG_CUDA(cudaMalloc(&L.d_class_patches, sizeof(int) * grouped.size()));
   DCG_CUDA(cudaMalloc(&L.d_work, sizeof(int) * work.size()));
   DCG_CUDA(cudaMalloc(&L.d_classes, sizeof(RasClass) * L.nclass));
   DCG_CUDA(cudaMemcpyAsync(L.d_patch_class, pclass.data(), sizeof(int) * L.npatch, cudaMemcpyHostToDevice, s));
-  DCG_CUDA(cudaMemcpyAsync(L.d_patch_yoff, yoff.data(), sizeof(long long) * L.npatch, cudaMemcpyHostToDevice, s));
   DCG_CUDA(cudaMemcpyAsync(L.d_class_patches, grouped.data(), sizeof(int) * grouped.size(), cudaMemcpyHostToDevice, s));
   DCG_CUDA(cudaMemcpyAsync(L.d_work, work.data(), sizeof(int) * work.size(), cudaMemcpyHostToDevice, s));
   DCG_CUDA(cudaMemcpyAsync(L.d_classes, L.classes.data(), sizeof(RasClass) * L.nclass, cudaMemcpyHostToDevice, s));
@@ -779,19 +880,20 @@ int coarse_solve_t(dcg_problem* p, const T* f, T* z, cudaStream_t s) {
   const T* lam = coarse_lam<T>(C);
   const long long ncols = nn / C.m;
   const dim3 grid((unsigned)((ncols + 31) / 32), (unsigned)((C.m + 31) / 32));
+  const size_t smem = sizeof(T) * 2 * 32 * (size_t)(C.m + 1);
   const long long in1 = 1, inm = C.m, inmm = (long long)C.m * C.m;
   if (D == 2) {
-    k_fdm_pass<T><<<grid, 256, 0, s>>>(f, tmp, S, nullptr, C.m, in1, ncols);
-    k_fdm_pass<T><<<grid, 256, 0, s>>>(tmp, z, S, lam, C.m, inm, ncols);
-    k_fdm_pass<T><<<grid, 256, 0, s>>>(z, tmp, S, nullptr, C.m, inm, ncols);
-    k_fdm_pass<T><<<grid, 256, 0, s>>>(tmp, z, S, nullptr, C.m, in1, ncols);
+    k_fdm_pass<T, true><<<grid, 256, smem, s>>>(f, tmp, S, nullptr, C.m, in1, ncols);
+    k_fdm_pass<T, false><<<grid, 256, smem, s>>>(tmp, z, S, lam, C.m, inm, ncols);
+    k_fdm_pass<T, false><<<grid, 256, smem, s>>>(z, tmp, S, nullptr, C.m, inm, ncols);
+    k_fdm_pass<T, true><<<grid, 256, smem, s>>>(tmp, z, S, nullptr, C.m, in1, ncols);
   } else {
-    k_fdm_pass<T><<<grid, 256, 0, s>>>(f, tmp, S, nullptr, C.m, in1, ncols);
-    k_fdm_pass<T><<<grid, 256, 0, s>>>(tmp, z, S, nullptr, C.m, inm, ncols);
-    k_fdm_pass<T><<<grid, 256, 0, s>>>(z, tmp, S, lam, C.m, inmm, ncols);
-    k_fdm_pass<T><<<grid, 256, 0, s>>>(tmp, z, S, nullptr, C.m, inmm, ncols);
-    k_fdm_pass<T><<<grid, 256, 0, s>>>(z, tmp, S, nullptr, C.m, inm, ncols);
-    k_fdm_pass<T><<<grid, 256, 0, s>>>(tmp, z, S, nullptr, C.m, in1, ncols);
+    k_fdm_pass<T, true><<<grid, 256, smem, s>>>(f, tmp, S, nullptr, C.m, in1, ncols);
+    k_fdm_pass<T, false><<<grid, 256, smem, s>>>(tmp, z, S, nullptr, C.m, inm, ncols);
+    k_fdm_pass<T, false><<<grid, 256, smem, s>>>(z, tmp, S, lam, C.m, inmm, ncols);
+    k_fdm_pass<T, false><<<grid, 256, smem, s>>>(tmp, z, S, nullptr, C.m, inmm, ncols);
+    k_fdm_pass<T, false><<<grid, 256, smem, s>>>(z, tmp, S, nullptr, C.m, inm, ncols);
+    k_fdm_pass<T, true><<<grid, 256, smem, s>>>(tmp, z, S, nullptr, C.m, in1, ncols);
   }
   note_launches(2 * D - 1);  // the check below counts one
   DCG_LAUNCH_CHECK();
@@ -803,14 +905,15 @@ int coarse_solve_t(dcg_problem* p, const T* f, T* z, cudaStream_t s) {
 template <typename T, int D>
 int ras_step_t(dcg_problem* p, Level& L, cudaStream_t s) {
   RasArgs ra{};
-  ra.m = L.m; ra.ntile = L.tiles.ntile;
-  ra.work = L.d_work; ra.class_patches = L.d_class_patches; ra.classes = L.d_classes; ra.yoff = L.d_patch_yoff;
-  ra.origin = L.d_origin; ra.local = L.d_local; ra.axis_tab = L.d_axis_tab; ra.axis_len = L.d_axis_len;
+  ra.m = L.m;
+  ra.work = L.d_work; ra.class_patches = L.d_class_patches; ra.classes = L.d_classes;
+  ra.origin = L.d_origin; ra.core = L.d_core; ra.local = L.d_local; ra.axis_tab = L.d_axis_tab;
+  ra.err = p->scal + S_ERR;
   ra.nwork = L.nwork;
   ra.g_off = ras_goff<T>(L.npmax);
   const size_t smem = ras_smem_bytes<T>(L.npmax);
   const bool resident = ras_resident<T>(L.npmax);
-  const int per_sm = std::max(1, (int)((227 * 1024) / (smem + 1024)));
+  const int per_sm = std::max(1, std::min(2048 / kRasThreads, (int)((227 * 1024) / (smem + 1024))));
   const int cap = 152 * per_sm;
   ra.items_per_cta = (L.nwork + cap - 1) / cap;
   int grid = (L.nwork + ra.items_per_cta - 1) / ra.items_per_cta;
@@ -1053,18 +1156,27 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
       DCG_LAUNCH_CHECK();
     }
   }
-  // RAS kernel shared memory opt-in (largest configuration of each variant)
+  // RAS kernel shared memory opt-in: 227 KB per block minus the kernel's
+  // static shared memory
   {
-    const int big = 227 * 1024;
-    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<float, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<float, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<float, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<float, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<double, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<double, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<double, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    DCG_CUDA(cudaFuncSetAttribute(k_ras_solve<double, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    const size_t need = (fp32 ? sizeof(float) : sizeof(double)) * 2 * 32 * (size_t)(p->coarse.m + 1);
+    if (need > 220 * 1024) {
+      set_error_msg("coarsest level too large for the fast-diagonalisation panels (use more levels)");
+      return DCG_ERR_UNSUPPORTED;
+    }
+    DCG_TRY(set_ras_smem(k_fdm_pass<float, true>));
+    DCG_TRY(set_ras_smem(k_fdm_pass<float, false>));
+    DCG_TRY(set_ras_smem(k_fdm_pass<double, true>));
+    DCG_TRY(set_ras_smem(k_fdm_pass<double, false>));
   }
+  DCG_TRY(set_ras_smem(k_ras_solve<float, 2, true>));
+  DCG_TRY(set_ras_smem(k_ras_solve<float, 3, true>));
+  DCG_TRY(set_ras_smem(k_ras_solve<float, 2, false>));
+  DCG_TRY(set_ras_smem(k_ras_solve<float, 3, false>));
+  DCG_TRY(set_ras_smem(k_ras_solve<double, 2, true>));
+  DCG_TRY(set_ras_smem(k_ras_solve<double, 3, true>));
+  DCG_TRY(set_ras_smem(k_ras_solve<double, 2, false>));
+  DCG_TRY(set_ras_smem(k_ras_solve<double, 3, false>));
   DCG_CUDA(cudaStreamSynchronize(s));
   if (!exact_mode(p)) DCG_TRY(build_wcycle_graph(p));
   return DCG_OK;

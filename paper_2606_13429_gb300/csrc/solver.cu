@@ -292,6 +292,10 @@ int read_scalars(dcg_problem* p, cudaStream_t s) {
   DCG_CUDA(cudaMemcpyAsync(p->scal_host, p->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
   DCG_CUDA(cudaStreamSynchronize(s));
   if (p->prof.mask) prof_flush(p);
+  if (p->scal_host[S_ERR] != 0.0) {
+    set_error_msg("a bounded device wait gave up (bulk copy did not complete)");
+    return DCG_ERR_CUDA;
+  }
   return DCG_OK;
 }
 
