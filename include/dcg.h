@@ -219,6 +219,27 @@ int dcg_profile_enable(dcg_problem* p, unsigned mask, void* stream);
 int dcg_profile_read(dcg_problem* p, int cls, double* ms, long long* launches, double* flops, double* bytes,
                      void* stream);
 
+/* ---- allocation-free coarsest solve ------------------------------------ */
+/* The paper has no counterpart of this entry point: it is a service for
+ * callers that cannot allocate device memory when they need the solve (a
+ * process whose device memory a caching allocator has already reserved, or a
+ * latency-critical loop that must not take an allocation's implicit
+ * synchronisation).
+ *
+ * dcg_coarse_solve_static computes z = Z_1^-1 f on the coarsest level like
+ * dcg_coarse_solve, always in FP64, and allocates nothing: the intermediate
+ * vector lives in a fixed array of DCG_STATIC_COARSE_MAX doubles (1 MiB)
+ * compiled into the library, which every GPU that loads the library keeps
+ * until the process exits. f_dev, z_dev: distinct device arrays of the
+ * coarsest level's node count (layout as the scalar vectors above; the
+ * caller owns them). A coarsest level with more than DCG_STATIC_COARSE_MAX
+ * nodes is rejected with DCG_ERR_INVALID_ARG and a message. The first call on
+ * a device looks the array's device address up (cudaGetSymbolAddress); make
+ * it before any stream capture. All calls share the array: calls whose work
+ * overlaps on the GPU race and must be serialised by the caller. */
+#define DCG_STATIC_COARSE_MAX 131072
+int dcg_coarse_solve_static(dcg_problem* p, const double* f_dev, double* z_dev, void* stream);
+
 /* Number of kernels this library has launched in the process so far (a
  * replay of the captured W-cycle graph counts each of its kernel nodes). */
 long long dcg_kernel_launches(void);

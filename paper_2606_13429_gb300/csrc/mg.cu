@@ -1315,3 +1315,94 @@ int mg_coarse_hook(dcg_problem* p, const double* f, double* z, cudaStream_t s) {
 }
 
 }  // namespace dcg
+
+// ---------------------------------------------------------------------------
+// Allocation-free exact coarsest solve.
+//
+// dcg_coarse_solve keeps its intermediate vectors in buffers that dcg_setup
+// allocated. This variant allocates nothing at all: the one intermediate
+// vector between the fast-diagonalisation passes lives in the fixed device
+// array below, compiled into the library (1 MiB; every GPU that loads the
+// library holds it until the process exits). It is meant for callers that
+// cannot call cudaMalloc at the point where they need the solve, for example
+// code running under a fixed device-memory budget that a caching allocator
+// has already reserved, or a latency-critical loop in which an allocation's
+// implicit synchronisation is not acceptable.
+//
+// The device address of the array is looked up once per device, on the first
+// call made with that device current (cudaGetSymbolAddress); make that first
+// call before any stream capture. All calls share the array: two calls whose
+// work overlaps on the GPU (different streams, or different threads) race on
+// it and must be serialised by the caller. Every element the passes read is
+// written earlier in the same call, so no clearing is needed.
+// ---------------------------------------------------------------------------
+namespace dcg {
+namespace {
+static __device__ __align__(256) double g_static_coarse_tmp[DCG_STATIC_COARSE_MAX];
+constexpr int kMaxDevices = 64;
+double* g_static_coarse_ptr[kMaxDevices] = {};
+}  // namespace
+}  // namespace dcg
+
+extern "C" int dcg_coarse_solve_static(dcg_problem* p, const double* f_dev, double* z_dev, void* stream) {
+  using namespace dcg;
+  if (!p || !f_dev || !z_dev || f_dev == z_dev) {
+    set_error_msg("dcg_coarse_solve_static: need a problem and distinct f, z device arrays");
+    return DCG_ERR_INVALID_ARG;
+  }
+  if (!p->is_setup || p->levels.empty()) {
+    set_error_msg("dcg_coarse_solve_static before dcg_setup of a deflated solver");
+    return DCG_ERR_STATE;
+  }
+  const Coarse& C = p->coarse;
+  const int D = p->dim;
+  const long long nn = ipow(C.m, D);
+  if (nn > (long long)DCG_STATIC_COARSE_MAX) {
+    char buf[200];
+    snprintf(buf, sizeof buf,
+             "dcg_coarse_solve_static: coarsest level has %lld nodes, more than the fixed scratch of %d "
+             "(DCG_STATIC_COARSE_MAX); use dcg_coarse_solve or more multigrid levels", nn,
+             (int)DCG_STATIC_COARSE_MAX);
+    set_error_msg(buf);
+    return DCG_ERR_INVALID_ARG;
+  }
+  const size_t smem = sizeof(double) * 2 * 32 * (size_t)(C.m + 1);
+  if (smem > 220 * 1024) {
+    set_error_msg("dcg_coarse_solve_static: coarsest level too large for the pass panels");
+    return DCG_ERR_UNSUPPORTED;
+  }
+  int dev = 0;
+  DCG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error_msg("dcg_coarse_solve_static: device index out of range");
+    return DCG_ERR_UNSUPPORTED;
+  }
+  if (!g_static_coarse_ptr[dev]) {
+    void* ptr = nullptr;
+    DCG_CUDA(cudaGetSymbolAddress(&ptr, g_static_coarse_tmp));
+    g_static_coarse_ptr[dev] = static_cast<double*>(ptr);
+  }
+  double* tmp = g_static_coarse_ptr[dev];
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long ncols = nn / C.m;
+  const dim3 grid((unsigned)((ncols + 31) / 32), (unsigned)((C.m + 31) / 32));
+  const long long in1 = 1, inm = C.m, inmm = (long long)C.m * C.m;
+  const double* S = C.S64;
+  const double* lam = C.lam64;
+  if (D == 2) {
+    k_fdm_pass<double, true><<<grid, 256, smem, s>>>(f_dev, tmp, S, nullptr, C.m, in1, ncols);
+    k_fdm_pass<double, false><<<grid, 256, smem, s>>>(tmp, z_dev, S, lam, C.m, inm, ncols);
+    k_fdm_pass<double, false><<<grid, 256, smem, s>>>(z_dev, tmp, S, nullptr, C.m, inm, ncols);
+    k_fdm_pass<double, true><<<grid, 256, smem, s>>>(tmp, z_dev, S, nullptr, C.m, in1, ncols);
+  } else {
+    k_fdm_pass<double, true><<<grid, 256, smem, s>>>(f_dev, tmp, S, nullptr, C.m, in1, ncols);
+    k_fdm_pass<double, false><<<grid, 256, smem, s>>>(tmp, z_dev, S, nullptr, C.m, inm, ncols);
+    k_fdm_pass<double, false><<<grid, 256, smem, s>>>(z_dev, tmp, S, lam, C.m, inmm, ncols);
+    k_fdm_pass<double, false><<<grid, 256, smem, s>>>(tmp, z_dev, S, nullptr, C.m, inmm, ncols);
+    k_fdm_pass<double, false><<<grid, 256, smem, s>>>(z_dev, tmp, S, nullptr, C.m, inm, ncols);
+    k_fdm_pass<double, true><<<grid, 256, smem, s>>>(tmp, z_dev, S, nullptr, C.m, in1, ncols);
+  }
+  note_launches(2 * D - 1);
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}

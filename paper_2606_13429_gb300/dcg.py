@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
         "dcg_profile_enable": (I, [P, C.c_uint, VP]),
         "dcg_profile_read": (I, [P, I, C.POINTER(D), C.POINTER(LL), C.POINTER(D), C.POINTER(D), VP]),
         "dcg_kernel_launches": (LL, []),
+        "dcg_coarse_solve_static": (I, [P, VP, VP, VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -327,6 +328,12 @@ def dcg_profile_read(prob: Problem, stream=None) -> dict:
                                        _stream(stream)), "dcg_profile_read")
         out[name] = {"ms": ms.value, "launches": n.value, "flops": fl.value, "bytes": by.value}
     return out
+
+
+def dcg_coarse_solve_static(prob: Problem, f, z, stream=None):
+    """Allocation-free coarsest solve (fixed device scratch inside the library)."""
+    _check(load().dcg_coarse_solve_static(prob.ptr, _dptr(f, name="f"), _dptr(z, name="z"), _stream(stream)),
+           "dcg_coarse_solve_static")
 
 
 def dcg_kernel_launches() -> int:
