@@ -136,7 +136,9 @@ struct Tiles1D {
 struct RasClass {
   int len[kMaxDim];   // box extent per axis
   int np;             // prod(len)
+  int npp;            // np rounded up to a multiple of 4 (row length of the stored inverse)
   int local_off;      // offset of the class's packed local coordinates
+  int nb;             // boxes per work item (batch width of the product)
   long long inv_off;  // offset of the inverse in the level's inverse array
 };
 
@@ -157,15 +159,20 @@ struct Level {
   int* d_local = nullptr;           // packed local coordinates of every class
   int4* d_axis_tab = nullptr;       // [m] boxes containing each coordinate
   int2* d_core = nullptr;           // [npatch] core tile in box-local coordinates
+  int* d_local_node = nullptr;      // per class: node offset of each local node from the box origin
+  long long* d_item_off = nullptr;  // [nwork] offset of each work item's results in y
+  int* d_ysrc = nullptr;            // [nn * 2^d] index in y of each node's box results, -1 = none
+  void* r = nullptr;                // residual f - Z z (cycle precision)
   int nwork = 0;
   long long ylen = 0;
   long long ras_np2 = 0;            // sum over boxes of np^2 (FMAs of one smoothing product)
+  long long gmax = 0;               // max over classes of np * nb (residual tile elements)
   void* d_inv = nullptr;            // inverses in the W-cycle precision (row-major, symmetric)
   void* d_inv_bf16 = nullptr;       // optional BF16 copy
   // vectors in the W-cycle precision
   void* f = nullptr;
   void* z = nullptr;
-  void* y = nullptr;                // RAS box results, node-major (2^d slots per node)
+  void* y = nullptr;                // RAS box results, work-item layout [item][np][nb]
 };
 
 struct Coarse {

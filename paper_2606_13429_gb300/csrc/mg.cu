@@ -40,10 +40,8 @@
 namespace dcg {
 namespace {
 
-constexpr int kNB = 32;       // boxes per CTA batch in the RAS GEMM
 constexpr int kKC = 32;       // K chunk of the inverse staged in shared memory
-constexpr int kRasThreads = 1024;  // 32 warps per work item: latency hiding on sparse levels
-constexpr int kRowGroups = kRasThreads / 8;  // row groups of the GEMM (8 groups of 4 boxes)
+constexpr int kRasThreads = 256;
 constexpr int kMaxNp = 256;   // largest box (nodes) supported
 
 // ---------------------------------------------------------------------------
@@ -176,12 +174,13 @@ __global__ void k_gauss_jordan(double* __restrict__ a, int n) {
   }
 }
 
+// symmetrised inverse in the cycle precision, rows padded to npp (zeros)
 template <typename T>
-__global__ void k_sym_convert(const double* __restrict__ a, T* __restrict__ out, int n) {
+__global__ void k_sym_convert(const double* __restrict__ a, T* __restrict__ out, int n, int npp) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)n * n) return;
-  int i = (int)(t / n), j = (int)(t % n);
-  out[t] = (T)(0.5 * (a[t] + a[(long long)j * n + i]));
+  if (t >= (long long)n * npp) return;
+  int i = (int)(t / npp), j = (int)(t % npp);
+  out[t] = j < n ? (T)(0.5 * (a[(long long)i * n + j] + a[(long long)j * n + i])) : (T)0;
 }
 
 // sine basis S[i][j] = sqrt(2/(m+1)) sin((i+1)(j+1) pi/(m+1)) and eigenvalues
@@ -339,6 +338,8 @@ struct RasArgs {
   const int4* origin;        // [npatch] box origin (x, y, z) and its node index
   const int2* core;          // [npatch] core tile in box-local coordinates, packed 10 bits per axis (lo, hi)
   const int* local;          // per class: packed local coordinates, 10 bits per axis
+  const int* local_off_node; // per class: node offset of each local node from the box origin node
+  const long long* item_off; // [nwork] offset of each work item's results in y
   const int4* axis_tab;      // [m] per coordinate: (t0, l0, t1, l1), t1 = -1 when one box only
   int nwork;
   int items_per_cta;
@@ -357,16 +358,32 @@ constexpr int slots_per_node() { return 1 << D; }
 // A CTA walks a contiguous range of work items (sorted by class); when
 // RESIDENT, the class inverse is brought into shared memory with one bulk
 // asynchronous copy while the residuals are gathered, and kept while the
-// class does not change.
+// class does not change. GEMM Y[np x nb] = inv[np x np] G[np x nb]: thread
+// (ty, tx) owns rows 4ty..4ty+3 and boxes 8tx..8tx+7 (16-byte shared loads);
+// the class's batch width nb_c = 8 * bg with bg * ceil(np/4) <= threads.
+template <typename T>
+struct Vec4 { using type = float4; };
+template <>
+struct Vec4<double> { using type = double4; };
+
+template <typename T>
+__device__ __forceinline__ void lds4(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+}
+
 template <typename T, int D, bool RESIDENT>
-__global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, Stencil<T> st, const T* __restrict__ f,
-                                                            const T* __restrict__ z, const T* __restrict__ inv,
-                                                            T* __restrict__ y) {
+__global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, const T* __restrict__ rvec,
+                                                            const T* __restrict__ inv, T* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   const int tid = threadIdx.x;
-  const int tx = tid & 7;   // group of 4 boxes
-  const int ty = tid >> 3;  // rows ty, ty+kRowGroups, ...
   const int w0 = blockIdx.x * ra.items_per_cta;
   const int w1 = min(ra.nwork, w0 + ra.items_per_cta);
   if (RESIDENT) {
@@ -375,75 +392,74 @@ __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, Stencil<T
   }
   unsigned phase = 0;
   int cur_cls = -1;
-  constexpr int SL = slots_per_node<D>();
   for (int w = w0; w < w1; ++w) {
     const int cls = ra.work[3 * w], first = ra.work[3 * w + 1], nb = ra.work[3 * w + 2];
     const RasClass C = ra.classes[cls];
     const int np = C.np;
-    T* As = reinterpret_cast<T*>(smem_raw);                 // RESIDENT: [np][np], else [kKC][np]
-    T* G = As + ra.g_off;                                   // [np][kNB]
+    const int npp = C.npp;                                  // padded row length of the inverse (multiple of 4)
+    const int NB = C.nb;                                    // batch width of the class (power of 2, <= 256)
+    const int bg = NB >> 3;                                 // box groups of 8
+    const int rg = (np + 3) >> 2;                           // row groups of 4
+    T* As = reinterpret_cast<T*>(smem_raw);                 // RESIDENT: [np][npp], else [kKC][npp]
+    T* G = As + ra.g_off;                                   // [np][NB]
     __syncthreads();
     bool loading = false;
     if (RESIDENT && cls != cur_cls) {
       if (tid == 0) {
-        const unsigned bytes = (unsigned)((((size_t)np * np * sizeof(T)) + 15) & ~(size_t)15);
+        const unsigned bytes = (unsigned)((size_t)np * npp * sizeof(T));  // multiple of 16
         mbar_expect_tx(&bar, bytes);
         tma_load_1d(As, inv + C.inv_off, bytes, &bar);
       }
       loading = true;
       cur_cls = cls;
     }
-    // gather residuals f - Z z on the boxes: thread keeps box b = tid % kNB
-    // and walks local nodes k = tid / kNB + j * (threads / kNB)
+    // gather the residual (computed once per node beforehand) on the boxes:
+    // thread keeps box b = tid % NB; one load per box node
     {
-      const int b = tid % kNB;
-      const int kstep = blockDim.x / kNB;
-      int4 o4 = make_int4(0, 0, 0, 0);
-      if (b < nb) o4 = __ldg(ra.origin + __ldg(ra.class_patches + first + b));
-#pragma unroll 6
-      for (int k = tid / kNB; k < np; k += kstep) {
+      const int b = tid & (NB - 1);
+      const int kstep = kRasThreads / NB;
+      int node0 = 0;
+      if (b < nb) node0 = __ldg(ra.origin + __ldg(ra.class_patches + first + b)).w;
+#pragma unroll 8
+      for (int k = tid / NB; k < np; k += kstep) {
         T r = 0;
-        if (b < nb) {
-          const int pk = __ldg(ra.local + C.local_off + k);
-          const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = (pk >> 20) & 1023;
-          int c[3] = {o4.x + lx, o4.y + ly, o4.z + lz};
-          const long long a = (long long)o4.w + lx + (long long)ra.m * (ly + (D > 2 ? (long long)ra.m * lz : 0));
-          r = __ldg(f + a) - stencil_apply<T, D>(st, z, ra.m, c);
-        }
-        G[(size_t)k * kNB + b] = r;
+        if (b < nb) r = __ldg(rvec + node0 + __ldg(ra.local_off_node + C.local_off + k));
+        G[(size_t)k * NB + b] = r;
       }
     }
     bool ok = true;
     if (loading) {
-      // every thread waits (bounded) for the bulk copy it is about to read;
-      // a second bounded wait lets a slow copy in flight finish
       ok = mbar_wait_bounded(&bar, phase) || mbar_wait_bounded(&bar, phase);
       phase ^= 1u;
     }
-    constexpr int RI = (kMaxNp + kRowGroups - 1) / kRowGroups;
-    T acc[RI][4];
+    const int tx = tid % bg, ty = tid / bg;
+    const bool active = ty < rg;
+    T acc[4][8];
 #pragma unroll
-    for (int r = 0; r < RI; ++r)
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = 0;
+      for (int c = 0; c < 8; ++c) acc[r][c] = 0;
     if (RESIDENT) {
       if (__syncthreads_or(!ok)) {  // uniform decision after the barrier
         if (tid == 0) *ra.err = 1.0;
         return;
       }
-      for (int kk = 0; kk < np; ++kk) {
-        const T* g = G + (size_t)kk * kNB + 4 * tx;
-        const T g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3];
-        const T* arow = As + (size_t)kk * np;
+      if (active) {
+        const T* gcol = G + 8 * tx;
+        const T* acol = As + 4 * ty;
+#pragma unroll 2
+        for (int kk = 0; kk < np; ++kk) {
+          T av[4], g0[4], g1[4];
+          lds4(acol + (size_t)kk * npp, av);
+          lds4(gcol + (size_t)kk * NB, g0);
+          lds4(gcol + (size_t)kk * NB + 4, g1);
 #pragma unroll
-        for (int r = 0; r < RI; ++r) {
-          const int i = ty + kRowGroups * r;
-          if (i < np) {
-            const T av = arow[i];
-            acc[r][0] += av * g0;
-            acc[r][1] += av * g1;
-            acc[r][2] += av * g2;
-            acc[r][3] += av * g3;
+          for (int r = 0; r < 4; ++r) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              acc[r][c] = fma(av[r], g0[c], acc[r][c]);
+              acc[r][c + 4] = fma(av[r], g1[c], acc[r][c + 4]);
+            }
           }
         }
       }
@@ -453,92 +469,87 @@ __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, Stencil<T
         const int kc = min(kKC, np - k0);
         __syncthreads();
 #pragma unroll 8
-        for (int idx = tid; idx < kc * np; idx += blockDim.x) As[idx] = __ldg(invc + (size_t)k0 * np + idx);
+        for (int idx = tid; idx < kc * npp; idx += blockDim.x) As[idx] = __ldg(invc + (size_t)k0 * npp + idx);
         __syncthreads();
-        for (int kk = 0; kk < kc; ++kk) {
-          const T* g = G + (size_t)(k0 + kk) * kNB + 4 * tx;
-          const T g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3];
-          const T* arow = As + (size_t)kk * np;
+        if (active) {
+          const T* gcol = G + 8 * tx;
+          for (int kk = 0; kk < kc; ++kk) {
+            T av[4], g0[4], g1[4];
+            lds4(As + (size_t)kk * npp + 4 * ty, av);
+            lds4(gcol + (size_t)(k0 + kk) * NB, g0);
+            lds4(gcol + (size_t)(k0 + kk) * NB + 4, g1);
 #pragma unroll
-          for (int r = 0; r < RI; ++r) {
-            const int i = ty + kRowGroups * r;
-            if (i < np) {
-              const T av = arow[i];
-              acc[r][0] += av * g0;
-              acc[r][1] += av * g1;
-              acc[r][2] += av * g2;
-              acc[r][3] += av * g3;
+            for (int r = 0; r < 4; ++r) {
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                acc[r][c] = fma(av[r], g0[c], acc[r][c]);
+                acc[r][c + 4] = fma(av[r], g1[c], acc[r][c + 4]);
+              }
             }
           }
         }
       }
     }
-    // epilogue: node-major results with the box's slot per node
+    // epilogue: results in the work item's layout y[item][i][NB] (8
+    // consecutive boxes per thread row: two 16-byte stores)
+    if (active) {
+      T* yi = y + ra.item_off[w];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int b = 4 * tx + c;
-      if (b >= nb) continue;
-      const int pid = __ldg(ra.class_patches + first + b);
-      const int4 o4 = __ldg(ra.origin + pid);
-      const int2 cb = __ldg(ra.core + pid);
-#pragma unroll
-      for (int r = 0; r < RI; ++r) {
-        const int i = ty + kRowGroups * r;
+      for (int r = 0; r < 4; ++r) {
+        const int i = 4 * ty + r;
         if (i < np) {
-          const int pk = __ldg(ra.local + C.local_off + i);
-          const int lx = pk & 1023, ly = (pk >> 10) & 1023, lz = (pk >> 20) & 1023;
-          int slot = (lx < (cb.x & 1023) || lx >= (cb.y & 1023)) ? 1 : 0;
-          slot |= (ly < ((cb.x >> 10) & 1023) || ly >= ((cb.y >> 10) & 1023)) ? 2 : 0;
-          if (D > 2) slot |= (lz < ((cb.x >> 20) & 1023) || lz >= ((cb.y >> 20) & 1023)) ? 4 : 0;
-          const long long a = (long long)o4.w + lx + (long long)ra.m * (ly + (D > 2 ? (long long)ra.m * lz : 0));
-          y[a * SL + slot] = acc[r][c];
+          T* dst = yi + (size_t)i * NB + 8 * tx;
+          if constexpr (sizeof(T) == 4) {
+            reinterpret_cast<float4*>(dst)[0] = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+            reinterpret_cast<float4*>(dst)[1] = make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 8; c += 2)
+              reinterpret_cast<double2*>(dst)[c / 2] = make_double2(acc[r][c], acc[r][c + 1]);
+          }
         }
       }
     }
   }
 }
 
-// (2) z[j] += D_j * sum of the box results stored for node j (node-major
-// slots; which slots exist comes from the per-coordinate table).
+// (2) z[j] += D_j * sum over the boxes containing j of their result for j;
+// ysrc[j * 2^D + slot] is the index of that result in y (-1: no such box),
+// slot bit ax = 0 for the node's own core tile along axis ax, 1 for the
+// neighbouring tile whose overlap reaches it. D_j = 1/multiplicity, or 0/1
+// on the core (restricted: slot 0 only).
 template <typename T, int D>
-__global__ void k_ras_update(RasArgs ra, const T* __restrict__ y, T* __restrict__ z, long long nn, int restricted) {
-  constexpr int SL = slots_per_node<D>();
+__global__ void k_ras_update(const int* __restrict__ ysrc, const T* __restrict__ y, T* __restrict__ z, long long nn,
+                             int restricted) {
+  constexpr int SL = 1 << D;
   for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nn; a += (long long)gridDim.x * blockDim.x) {
-    int c[3];
-    coords_of<D>(a, ra.m, c);
-    T v[SL];
-    if (sizeof(T) == 4 && SL >= 4) {
-#pragma unroll
-      for (int q = 0; q < SL; q += 4) {
-        const float4 t4 = __ldg(reinterpret_cast<const float4*>(y + a * SL + q));
-        v[q] = t4.x; v[q + 1] = t4.y; v[q + 2] = t4.z; v[q + 3] = t4.w;
-      }
+    int idx[SL];
+    if constexpr (SL == 4) {
+      const int4 t = __ldg(reinterpret_cast<const int4*>(ysrc) + a);
+      idx[0] = t.x; idx[1] = t.y; idx[2] = t.z; idx[3] = t.w;
     } else {
-#pragma unroll
-      for (int q = 0; q < SL; q += 2) {
-        const double2 t2 = __ldg(reinterpret_cast<const double2*>(y + a * SL + q));
-        v[q] = (T)t2.x; v[q + 1] = (T)t2.y;
-      }
+      const int4 t0 = __ldg(reinterpret_cast<const int4*>(ysrc) + 2 * a);
+      const int4 t1 = __ldg(reinterpret_cast<const int4*>(ysrc) + 2 * a + 1);
+      idx[0] = t0.x; idx[1] = t0.y; idx[2] = t0.z; idx[3] = t0.w;
+      idx[4] = t1.x; idx[5] = t1.y; idx[6] = t1.z; idx[7] = t1.w;
     }
-    T s = v[0];
+    T s = __ldg(y + idx[0]);
     int mult = 1;
     if (!restricted) {
-      int other[3] = {0, 0, 0};
 #pragma unroll
-      for (int q = 0; q < D; ++q) other[q] = __ldg(&ra.axis_tab[c[q]].z) >= 0;
-#pragma unroll
-      for (int sl = 1; sl < SL; ++sl) {
-        bool ok = true;
-#pragma unroll
-        for (int q = 0; q < D; ++q)
-          if ((sl >> q) & 1) ok = ok && other[q];
-        if (ok) s += v[sl];
-      }
-      mult = (1 + other[0]) * (1 + other[1]) * (D > 2 ? (1 + other[2]) : 1);
+      for (int sl = 1; sl < SL; ++sl)
+        if (idx[sl] >= 0) {
+          s += __ldg(y + idx[sl]);
+          ++mult;
+        }
     }
     z[a] += restricted ? s : s / (T)mult;
   }
 }
+
+// padded panel row length of the coarse passes: odd, so rows start in
+// different shared-memory banks
+__host__ __device__ inline int fdm_row(int m) { return (m % 2 == 1) ? m + 2 : m + 1; }
 
 // Coarsest solve pass: out = S applied along one axis, as the GEMM
 // C[i][n] = sum_j S[i][j] B[j][n] with B[j][n] = in[(n / inner) m inner + j inner + n % inner]
@@ -552,36 +563,34 @@ __global__ void __launch_bounds__(256) k_fdm_pass(const T* __restrict__ in, T* _
                                                    const T* __restrict__ S, const T* __restrict__ lam, int m,
                                                    long long inner, long long ncols) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int mp = m + 1;                                   // padded row length
+  const int mp = fdm_row(m);                              // odd padded row length: no bank conflicts
   T* sS = reinterpret_cast<T*>(smem_raw);                 // [32][mp]
   T* sB = sS + 32 * mp;                                   // AXIS0: [32][mp] (n-major), else [m][32]
   const int tid = threadIdx.x;
   const int i0 = blockIdx.y * 32;
   const unsigned n0 = blockIdx.x * 32u;
   const unsigned ui = (unsigned)inner;
-  // one load round: S rows i0..i0+31, B columns n0..n0+31
-#pragma unroll 4
-  for (int e = tid; e < 32 * m; e += 256) {
-    const int r = e / m, j = e - r * m;
-    const int ii = i0 + r;
-    sS[r * mp + j] = ii < m ? __ldg(S + (size_t)ii * m + j) : (T)0;
-    if (AXIS0) {
-      const unsigned nb = n0 + r;  // column r of the panel, element j
-      sB[r * mp + j] = nb < (unsigned)ncols ? __ldg(in + (size_t)nb * m + j) : (T)0;
+  // one load round: rows r = 0..31 of the S panel (and of the transposed B
+  // panel for axis 0), columns j = tid, tid+256, ... (no division)
+  for (int j = tid; j < m; j += 256) {
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+      const int ii = i0 + r;
+      sS[r * mp + j] = ii < m ? __ldg(S + (size_t)ii * m + j) : (T)0;
+      if (AXIS0) {
+        const unsigned nb = n0 + r;
+        sB[r * mp + j] = nb < (unsigned)ncols ? __ldg(in + (size_t)nb * m + j) : (T)0;
+      }
     }
   }
   if (!AXIS0) {
-#pragma unroll 4
-    for (int e = tid; e < 32 * m; e += 256) {
-      const int j = e >> 5, c = e & 31;
-      const unsigned nb = n0 + c;
-      T v = 0;
-      if (nb < (unsigned)ncols) {
-        const unsigned hi = nb / ui;
-        v = __ldg(in + (size_t)hi * m * ui + (size_t)j * ui + (nb - hi * ui));
-      }
-      sB[j * 32 + c] = v;
-    }
+    const int c = tid & 31;
+    const unsigned nb = n0 + c;
+    const bool okc = nb < (unsigned)ncols;
+    const unsigned hi = okc ? nb / ui : 0u;
+    const size_t base = (size_t)hi * m * ui + (nb - hi * ui);
+#pragma unroll 8
+    for (int j = tid >> 5; j < m; j += 8) sB[j * 32 + c] = okc ? __ldg(in + base + (size_t)j * ui) : (T)0;
   }
   __syncthreads();
   const int ti = tid >> 3, tn = (tid & 7) * 4;
@@ -694,23 +703,34 @@ int set_ras_smem(K kernel) {
   return DCG_OK;
 }
 
+// batch width of a box class: 8 boxes per thread column, as many columns as
+// fit 256 threads with ceil(np/4) row groups (power of two, 8..256 boxes)
+int class_batch(int np) {
+  const int rg = (np + 3) / 4;
+  int bg = 1;
+  while (bg * 2 * rg <= kRasThreads && bg * 2 <= 32) bg *= 2;
+  return 8 * bg;
+}
+
 template <typename T>
-bool ras_resident(int npmax) {
-  return sizeof(T) * ((size_t)npmax * npmax + (size_t)npmax * kNB) <= kResidentSmem;
+bool ras_resident(const Level& L) {
+  const size_t npp = (L.npmax + 3) / 4 * 4;
+  return sizeof(T) * ((size_t)L.npmax * npp + (size_t)L.gmax) <= kResidentSmem;
 }
 template <typename T>
-long long ras_goff(int npmax) {
-  // the bulk copy moves whole 16-byte chunks: round the inverse region up
-  return ras_resident<T>(npmax) ? ((long long)npmax * npmax + 3) / 4 * 4 : (long long)kKC * npmax;
+long long ras_goff(const Level& L) {
+  const long long npp = (L.npmax + 3) / 4 * 4;
+  return ras_resident<T>(L) ? (long long)L.npmax * npp : (long long)kKC * npp;
 }
 template <typename T>
-size_t ras_smem_bytes(int npmax) {
-  return sizeof(T) * ((size_t)ras_goff<T>(npmax) + (size_t)npmax * kNB);
+size_t ras_smem_bytes(const Level& L) {
+  return sizeof(T) * ((size_t)ras_goff<T>(L) + (size_t)L.gmax);
 }
 
 void free_level(Level& L) {
   cudaFree(L.d_patch_class); cudaFree(L.d_work); cudaFree(L.d_class_patches);
   cudaFree(L.d_classes); cudaFree(L.d_origin); cudaFree(L.d_core); cudaFree(L.d_local); cudaFree(L.d_axis_tab);
+  cudaFree(L.d_local_node); cudaFree(L.d_item_off); cudaFree(L.d_ysrc); cudaFree(L.r);
   cudaFree(L.d_inv); cudaFree(L.d_inv_bf16); cudaFree(L.f); cudaFree(L.z); cudaFree(L.y);
   L = Level{};
 }
@@ -745,7 +765,7 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
     }
     pclass[pid] = c;
   }
-  L.ylen = L.nn * (1LL << D);  // node-major results, 2^D slots per node
+
   L.ras_np2 = 0;
   for (int pid = 0; pid < L.npatch; ++pid) L.ras_np2 += (long long)L.classes[pclass[pid]].np * L.classes[pclass[pid]].np;
   L.nclass = (int)L.classes.size();
@@ -756,9 +776,12 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
       set_error_msg("RAS box larger than 256 nodes: reduce patch/overlap");
       return DCG_ERR_UNSUPPORTED;
     }
-    c.inv_off = inv_total;  // 16-byte aligned for the bulk copy into shared memory
-    inv_total += ((long long)c.np * c.np + 3) / 4 * 4;
+    c.npp = (c.np + 3) / 4 * 4;  // rows padded: 16-byte aligned vector loads
+    c.inv_off = inv_total;       // 16-byte aligned for the bulk copy into shared memory
+    inv_total += (long long)c.np * c.npp;
+    c.nb = class_batch(c.np);
     L.npmax = std::max(L.npmax, c.np);
+    L.gmax = std::max(L.gmax, (long long)c.np * c.nb);
   }
   // group patches by class, batch into work items
   std::vector<int> grouped;
@@ -768,10 +791,11 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
     for (int pid = 0; pid < L.npatch; ++pid)
       if (pclass[pid] == c) grouped.push_back(pid);
     int cnt = (int)grouped.size() - start;
-    for (int b = 0; b < cnt; b += kNB) {
+    const int nbc = L.classes[c].nb;
+    for (int b = 0; b < cnt; b += nbc) {
       work.push_back(c);
       work.push_back(start + b);
-      work.push_back(std::min(kNB, cnt - b));
+      work.push_back(std::min(nbc, cnt - b));
     }
   }
   L.nwork = (int)work.size() / 3;
@@ -791,12 +815,48 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
     origin[pid] = make_int4(o3[0], o3[1], o3[2], (int)node);
     core[pid] = make_int2(lo, hi);
   }
-  std::vector<int> local;
+  std::vector<int> local, local_node;
   for (auto& c : L.classes) {
     c.local_off = (int)local.size();
     for (int k = 0; k < c.np; ++k) {
       int lx = k % c.len[0], ly = (k / c.len[0]) % c.len[1], lz = k / (c.len[0] * c.len[1]);
       local.push_back(lx | (ly << 10) | (lz << 20));
+      local_node.push_back((int)(lx + (long long)L.m * (ly + (long long)L.m * lz)));
+    }
+  }
+  // work-item result offsets and, per node and slot, the index of its result
+  const int SL = 1 << D;
+  std::vector<long long> item_off(L.nwork);
+  long long ytot = 0;
+  for (int w = 0; w < L.nwork; ++w) {
+    const RasClass& c = L.classes[work[3 * w]];
+    item_off[w] = ytot;
+    ytot += (long long)c.np * c.nb;
+  }
+  L.ylen = ytot;
+  if (ytot >= (1LL << 31)) {
+    set_error_msg("RAS result buffer exceeds int32 indexing");
+    return DCG_ERR_UNSUPPORTED;
+  }
+  std::vector<int> ysrc((size_t)L.nn * SL, -1);
+  for (int w = 0; w < L.nwork; ++w) {
+    const RasClass& c = L.classes[work[3 * w]];
+    const int first = work[3 * w + 1], cnt = work[3 * w + 2];
+    for (int b = 0; b < cnt; ++b) {
+      const int pid = grouped[first + b];
+      const int4 o4 = origin[pid];
+      const int2 cb = core[pid];
+      for (int i = 0; i < c.np; ++i) {
+        const int pk = local[c.local_off + i];
+        const int l3[3] = {pk & 1023, (pk >> 10) & 1023, (pk >> 20) & 1023};
+        int slot = 0;
+        for (int k = 0; k < D; ++k) {
+          const int lo = (cb.x >> (10 * k)) & 1023, hi = (cb.y >> (10 * k)) & 1023;
+          if (l3[k] < lo || l3[k] >= hi) slot |= 1 << k;
+        }
+        const long long node = o4.w + (long long)local_node[c.local_off + i];
+        ysrc[(size_t)node * SL + slot] = (int)(item_off[w] + (long long)i * c.nb + b);
+      }
     }
   }
   std::vector<int4> axis_tab(L.m);
@@ -811,6 +871,12 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
   }
   DCG_CUDA(cudaMalloc(&L.d_origin, sizeof(int4) * L.npatch));
   DCG_CUDA(cudaMalloc(&L.d_local, sizeof(int) * local.size()));
+  DCG_CUDA(cudaMalloc(&L.d_local_node, sizeof(int) * local_node.size()));
+  DCG_CUDA(cudaMalloc(&L.d_item_off, sizeof(long long) * item_off.size()));
+  DCG_CUDA(cudaMalloc(&L.d_ysrc, sizeof(int) * ysrc.size()));
+  DCG_CUDA(cudaMemcpyAsync(L.d_local_node, local_node.data(), sizeof(int) * local_node.size(), cudaMemcpyHostToDevice, s));
+  DCG_CUDA(cudaMemcpyAsync(L.d_item_off, item_off.data(), sizeof(long long) * item_off.size(), cudaMemcpyHostToDevice, s));
+  DCG_CUDA(cudaMemcpyAsync(L.d_ysrc, ysrc.data(), sizeof(int) * ysrc.size(), cudaMemcpyHostToDevice, s));
   DCG_CUDA(cudaMalloc(&L.d_axis_tab, sizeof(int4) * L.m));
   DCG_CUDA(cudaMalloc(&L.d_core, sizeof(int2) * L.npatch));
   DCG_CUDA(cudaMemcpyAsync(L.d_core, core.data(), sizeof(int2) * L.npatch, cudaMemcpyHostToDevice, s));
@@ -840,13 +906,15 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
     DCG_LAUNCH_CHECK();
     k_gauss_jordan<<<1, 1024, sizeof(double) * np, s>>>(work64, np);
     DCG_LAUNCH_CHECK();
-    if (fp32) k_sym_convert<float><<<g, 256, 0, s>>>(work64, (float*)L.d_inv + c.inv_off, np);
-    else k_sym_convert<double><<<g, 256, 0, s>>>(work64, (double*)L.d_inv + c.inv_off, np);
+    const int gp = (int)(((long long)np * c.npp + 255) / 256);
+    if (fp32) k_sym_convert<float><<<gp, 256, 0, s>>>(work64, (float*)L.d_inv + c.inv_off, np, c.npp);
+    else k_sym_convert<double><<<gp, 256, 0, s>>>(work64, (double*)L.d_inv + c.inv_off, np, c.npp);
     DCG_LAUNCH_CHECK();
   }
   DCG_CUDA(cudaStreamSynchronize(s));
   cudaFree(work64);
   DCG_CUDA(cudaMalloc(&L.y, tsz * L.ylen));
+  DCG_CUDA(cudaMalloc(&L.r, tsz * L.nn));
   return DCG_OK;
 }
 
@@ -880,7 +948,7 @@ int coarse_solve_t(dcg_problem* p, const T* f, T* z, cudaStream_t s) {
   const T* lam = coarse_lam<T>(C);
   const long long ncols = nn / C.m;
   const dim3 grid((unsigned)((ncols + 31) / 32), (unsigned)((C.m + 31) / 32));
-  const size_t smem = sizeof(T) * 2 * 32 * (size_t)(C.m + 1);
+  const size_t smem = sizeof(T) * 2 * 32 * (size_t)fdm_row(C.m);
   const long long in1 = 1, inm = C.m, inmm = (long long)C.m * C.m;
   if (D == 2) {
     k_fdm_pass<T, true><<<grid, 256, smem, s>>>(f, tmp, S, nullptr, C.m, in1, ncols);
@@ -903,59 +971,69 @@ int coarse_solve_t(dcg_problem* p, const T* f, T* z, cudaStream_t s) {
 }
 
 template <typename T, int D>
-int ras_step_t(dcg_problem* p, Level& L, cudaStream_t s) {
+int ras_step_t(dcg_problem* p, Level& L, cudaStream_t s, bool z_zero = false) {
   RasArgs ra{};
   ra.m = L.m;
   ra.work = L.d_work; ra.class_patches = L.d_class_patches; ra.classes = L.d_classes;
   ra.origin = L.d_origin; ra.core = L.d_core; ra.local = L.d_local; ra.axis_tab = L.d_axis_tab;
+  ra.local_off_node = L.d_local_node; ra.item_off = L.d_item_off;
   ra.err = p->scal + S_ERR;
   ra.nwork = L.nwork;
-  ra.g_off = ras_goff<T>(L.npmax);
-  const size_t smem = ras_smem_bytes<T>(L.npmax);
-  const bool resident = ras_resident<T>(L.npmax);
+  ra.g_off = ras_goff<T>(L);
+  const size_t smem = ras_smem_bytes<T>(L);
+  const bool resident = ras_resident<T>(L);
   const int per_sm = std::max(1, std::min(2048 / kRasThreads, (int)((227 * 1024) / (smem + 1024))));
   const int cap = 152 * per_sm;
   ra.items_per_cta = (L.nwork + cap - 1) / cap;
   int grid = (L.nwork + ra.items_per_cta - 1) / ra.items_per_cta;
-  // algorithmic work: the shared-inverse products and the box data they touch
-  double flops = 0.0, bytes = 0.0;
-  for (const auto& c : L.classes) bytes += sizeof(T) * (double)c.np * c.np;
-  flops = 2.0 * (double)L.ras_np2;
-  bytes += sizeof(T) * 3.0 * (double)L.ylen;
+  // residual once per node (the first step from a zero iterate uses f itself)
+  const T* rvec = (const T*)L.f;
+  if (!z_zero) {
+    const int prof = prof_begin(p, PC_TRANSFER, s, g_capturing);
+    k_residual<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(st_of<T>(L), (const T*)L.f, (const T*)L.z, (T*)L.r,
+                                                               L.m, L.nn);
+    DCG_LAUNCH_CHECK();
+    prof_end(p, prof, s, 2.0 * ipow(3, D) * (double)L.nn, sizeof(T) * 3.0 * L.nn, g_capturing);
+    rvec = (const T*)L.r;
+  }
+  // algorithmic work: the shared-inverse products and the data they touch
+  double bytes = 0.0;
+  for (const auto& c : L.classes) bytes += sizeof(T) * (double)c.np * c.npp;
+  const double flops = 2.0 * (double)L.ras_np2;
+  bytes += sizeof(T) * 2.0 * (double)L.ylen;
   int prof = prof_begin(p, PC_RAS_SOLVE, s, g_capturing);
   if (resident)
-    k_ras_solve<T, D, true><<<grid, kRasThreads, smem, s>>>(ra, st_of<T>(L), (const T*)L.f, (const T*)L.z,
-                                                            (const T*)L.d_inv, (T*)L.y);
+    k_ras_solve<T, D, true><<<grid, kRasThreads, smem, s>>>(ra, rvec, (const T*)L.d_inv, (T*)L.y);
   else
-    k_ras_solve<T, D, false><<<grid, kRasThreads, smem, s>>>(ra, st_of<T>(L), (const T*)L.f, (const T*)L.z,
-                                                             (const T*)L.d_inv, (T*)L.y);
+    k_ras_solve<T, D, false><<<grid, kRasThreads, smem, s>>>(ra, rvec, (const T*)L.d_inv, (T*)L.y);
   DCG_LAUNCH_CHECK();
   prof_end(p, prof, s, flops, bytes, g_capturing);
   prof = prof_begin(p, PC_RAS_UPDATE, s, g_capturing);
-  k_ras_update<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(ra, (const T*)L.y, (T*)L.z, L.nn,
+  k_ras_update<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(L.d_ysrc, (const T*)L.y, (T*)L.z, L.nn,
                                                                 p->opts.ras_weights == DCG_RAS_RESTRICTED);
   DCG_LAUNCH_CHECK();
-  prof_end(p, prof, s, (double)L.ylen, sizeof(T) * ((double)L.ylen + 2.0 * L.nn), g_capturing);
+  prof_end(p, prof, s, (double)L.nn * (1 << D),
+           (double)L.nn * ((1 << D) * (4.0 + sizeof(T)) + 2.0 * sizeof(T)), g_capturing);
   return DCG_OK;
 }
 
 template <typename T, int D>
-int wcycle_t(dcg_problem* p, int k, cudaStream_t s) {
+int wcycle_t(dcg_problem* p, int k, cudaStream_t s, bool z_zero) {
   Level& L = p->levels[k - 1];
   if (k == 1) return coarse_solve_t<T, D>(p, (const T*)L.f, (T*)L.z, s);
   Level& Lc = p->levels[k - 2];
-  for (int i = 0; i < p->opts.m1; ++i) DCG_TRY((ras_step_t<T, D>(p, L, s)));
+  for (int i = 0; i < p->opts.m1; ++i) DCG_TRY((ras_step_t<T, D>(p, L, s, z_zero && i == 0)));
   int prof = prof_begin(p, PC_TRANSFER, s, g_capturing);
-  k_residual<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(st_of<T>(L), (const T*)L.f, (const T*)L.z, (T*)L.y, L.m,
+  k_residual<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(st_of<T>(L), (const T*)L.f, (const T*)L.z, (T*)L.r, L.m,
                                                              L.nn);
   DCG_LAUNCH_CHECK();
-  k_restrict<T, D><<<grid_for(Lc.nn, 256, 8192), 256, 0, s>>>((const T*)L.y, (T*)Lc.f, L.m, Lc.m, Lc.nn);
+  k_restrict<T, D><<<grid_for(Lc.nn, 256, 8192), 256, 0, s>>>((const T*)L.r, (T*)Lc.f, L.m, Lc.m, Lc.nn);
   DCG_LAUNCH_CHECK();
   prof_end(p, prof, s, 2.0 * (ipow(3, D) * (double)L.nn + ipow(3, D) * (double)Lc.nn),
            sizeof(T) * (4.0 * L.nn + Lc.nn), g_capturing);
   DCG_CUDA(cudaMemsetAsync(Lc.z, 0, sizeof(T) * Lc.nn, s));
-  DCG_TRY((wcycle_t<T, D>(p, k - 1, s)));
-  DCG_TRY((wcycle_t<T, D>(p, k - 1, s)));
+  DCG_TRY((wcycle_t<T, D>(p, k - 1, s, true)));
+  DCG_TRY((wcycle_t<T, D>(p, k - 1, s, false)));
   prof = prof_begin(p, PC_TRANSFER, s, g_capturing);
   k_prolong_add<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>((const T*)Lc.z, (T*)L.z, L.m, Lc.m, L.nn);
   DCG_LAUNCH_CHECK();
@@ -967,7 +1045,7 @@ int wcycle_t(dcg_problem* p, int k, cudaStream_t s) {
 template <typename T>
 int wcycle_dispatch(dcg_problem* p, cudaStream_t s) {
   const int J = (int)p->levels.size();
-  return p->dim == 2 ? wcycle_t<T, 2>(p, J, s) : wcycle_t<T, 3>(p, J, s);
+  return p->dim == 2 ? wcycle_t<T, 2>(p, J, s, true) : wcycle_t<T, 3>(p, J, s, true);
 }
 
 int build_wcycle_graph(dcg_problem* p) {
@@ -1159,7 +1237,7 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
   // RAS kernel shared memory opt-in: 227 KB per block minus the kernel's
   // static shared memory
   {
-    const size_t need = (fp32 ? sizeof(float) : sizeof(double)) * 2 * 32 * (size_t)(p->coarse.m + 1);
+    const size_t need = (fp32 ? sizeof(float) : sizeof(double)) * 2 * 32 * (size_t)fdm_row(p->coarse.m);
     if (need > 220 * 1024) {
       set_error_msg("coarsest level too large for the fast-diagonalisation panels (use more levels)");
       return DCG_ERR_UNSUPPORTED;
@@ -1366,7 +1444,7 @@ extern "C" int dcg_coarse_solve_static(dcg_problem* p, const double* f_dev, doub
     set_error_msg(buf);
     return DCG_ERR_INVALID_ARG;
   }
-  const size_t smem = sizeof(double) * 2 * 32 * (size_t)(C.m + 1);
+  const size_t smem = sizeof(double) * 2 * 32 * (size_t)fdm_row(C.m);
   if (smem > 220 * 1024) {
     set_error_msg("dcg_coarse_solve_static: coarsest level too large for the pass panels");
     return DCG_ERR_UNSUPPORTED;
