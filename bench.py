@@ -48,7 +48,7 @@ DTS = [1e-6, 1e-5, 1e-4]          # timed deflated-CG solves (one dt per step, c
 DTS_CG = [1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 1e-1]   # plain CG reported over the whole sweep
 WORKLOAD = ("2D unit square 1024x1024 Q1 pseudo-stress (4 comps/node, N=4,186,116, BSR 4x4 FP64), nu=1, "
             "deflated CG at dt in {1e-6,1e-5,1e-4} (one dt per step, cycling), RHS uniform[-1,1) seed 0, "
-            "tol 1e-8 true residual; DCG: FCG(1), c_F=0.01, W-cycle 4 levels, RAS 8x8 cores overlap 2, m1=m2=2; "
+            "tol 1e-8 true residual; DCG: FCG(1), c_F=0.01, W-cycle (levels autotuned), RAS 8x8 cores overlap 2, m1=m2=2; "
             "plain CG over dt 1e-6..1e-1 reported in extra")
 # Outer / in-iteration W-cycle counts per dt of this workload (mixed precision),
 # measured on GB300 by this bench; the parity tests hold device and oracle
@@ -137,7 +137,7 @@ def dist_init():
 # --------------------------------------------------------------------------- oracle timing
 
 
-def oracle_kernel_times(n=1024, P=8, o=2, dt=1e-6):
+def oracle_kernel_times(n=1024, P=8, o=2, dt=1e-6, levels=2):
     """Time the FP64 oracle at the bench size: one BSR SpMV and one W-cycle
     (single thread). Returns seconds for each and the sample description."""
     from oracle import fem, mg
@@ -145,7 +145,7 @@ def oracle_kernel_times(n=1024, P=8, o=2, dt=1e-6):
     asm = fem.assemble(2, n, dt)
     A = asm.matrix().tocsr()
     V = fem.V_matrix(asm.mesh)
-    H = mg.Hierarchy(2, n, mg.inner_matrix(V, A), mg.MGOptions(patch=P, overlap=o, m1=2, m2=2, max_levels=4))
+    H = mg.Hierarchy(2, n, mg.inner_matrix(V, A), mg.MGOptions(patch=P, overlap=o, m1=2, m2=2, max_levels=levels))
     x = inputs.rhs(0, asm.mesh.n_unknowns)
     g = inputs.rhs(1, asm.mesh.n_nodes)
     t0 = time.perf_counter()
@@ -191,9 +191,32 @@ def run_ours(args):
     n = args.n
     probs = {}
     for dt in DTS:
-        p = dcg.dcg_assemble(2, n, dt)
-        dcg.dcg_setup(p, opts)
-        probs[dt] = p
+        probs[dt] = dcg.dcg_assemble(2, n, dt)
+    # autotune the hierarchy depth on the first problem: time one inner solve
+    # to 1e-10 for each candidate level count and keep the fastest
+    tune = {}
+    g = torch.from_numpy(inputs.rhs(1, probs[DTS[0]].n_nodes)).cuda()
+    for levels in args.levels:
+        o = dcg.options(patch=8, overlap=2, m1=2, m2=2, max_levels=levels, precision=prec,
+                        inner_rule=dcg.DCG_INNER_FIXED, c=0.01, recurrence=dcg.DCG_FCG1)
+        try:
+            dcg.dcg_setup(probs[DTS[0]], o)
+        except dcg.DCGError:
+            continue
+        best = None
+        for _ in range(3):
+            z = torch.zeros_like(g)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dcg.dcg_mg_solve(probs[DTS[0]], g, z, 1e-10)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            best = t if best is None else min(best, t)
+        tune[levels] = best
+    best_levels = min(tune, key=tune.get)
+    opts.max_levels = best_levels
+    for dt in DTS:
+        dcg.dcg_setup(probs[dt], opts)
     N = probs[DTS[0]].N
     f = torch.from_numpy(inputs.rhs(0, N)).cuda()
     x = torch.zeros_like(f)
@@ -299,13 +322,22 @@ def run_ours(args):
     # all-FP64 deflated CG at the smallest dt (W-cycle in FP64 too)
     if not args.skip_fp64:
         pf = dcg.dcg_assemble(2, n, DTS[0])
-        dcg.dcg_setup(pf, dcg.options(patch=8, overlap=2, m1=2, m2=2, max_levels=4, precision=dcg.DCG_FP64))
+        fp64_levels = best_levels
+        while True:  # FP64 coarse panels need twice the shared memory: deepen if needed
+            try:
+                dcg.dcg_setup(pf, dcg.options(patch=8, overlap=2, m1=2, m2=2, max_levels=fp64_levels,
+                                              precision=dcg.DCG_FP64))
+                break
+            except dcg.DCGError:
+                fp64_levels += 1
+                if fp64_levels > 8:
+                    raise
         x.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st = dcg.dcg_solve(pf, f, x, tol=1e-8, max_it=args.max_it)
         torch.cuda.synchronize()
-        extra["dcg_all_fp64_dt1e-6"] = {"s": time.perf_counter() - t0, "outer_its": st["outer_its"],
+        extra["dcg_all_fp64_dt1e-6"] = {"s": time.perf_counter() - t0, "outer_its": st["outer_its"], "mg_levels": fp64_levels,
                                         "total_mg_cycles": st["total_mg_cycles"], "true_relres": st["true_relres"]}
         pf.close()
     extra["spmv_fp64"] = {"GB_per_s": sp["bytes"] / (sp["ms"] / 1e3) / 1e9, "ms": sp["ms"] / max(1, sp["launches"])}
@@ -316,7 +348,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
-        t_spmv, t_wc = oracle_kernel_times(n)
+        t_spmv, t_wc = oracle_kernel_times(n, levels=best_levels)
         counts = [(st["outer_its"], st["iter_mg_cycles"]) for _, st in timed]
         cpu = {"value": compose_solve_time(t_spmv, t_wc, counts, N), "unit": "s/solve", "cores": 1,
                "kind": "oracle",
@@ -335,6 +367,7 @@ def run_ours(args):
             "dtype": "f64 outer CG, f32 W-cycle" if prec == dcg.DCG_MIXED else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "mg_levels": best_levels, "mg_levels_tuning_s": {str(k): v for k, v in tune.items()},
                        "l2": "inputs larger than L2 (BSR matrix 1.2 GB per dt)", "precision": args.precision,
                        "all_converged": ok},
             "e2e": {"value": e2e_s, "unit": "s/solve", "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": N * 8},
@@ -397,7 +430,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     samples = []
     for k in range(args.warmup + args.steps):
-        t_spmv, t_wc = oracle_kernel_times(args.n)
+        t_spmv, t_wc = oracle_kernel_times(args.n, levels=args.ref_levels)
         if k >= args.warmup:
             samples.append((t_spmv, t_wc))
     t_spmv = statistics.median(s[0] for s in samples)
@@ -433,6 +466,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-cg", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--levels", type=int, nargs="+", default=[2, 3, 4], help="hierarchy depths to autotune over")
+    ap.add_argument("--ref-levels", type=int, default=2, help="hierarchy depth of the oracle in the reference arm")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
