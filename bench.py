@@ -196,9 +196,10 @@ def run_ours(args):
     # to 1e-10 for each candidate level count and keep the fastest
     tune = {}
     g = torch.from_numpy(inputs.rhs(1, probs[DTS[0]].n_nodes)).cuda()
-    for levels in args.levels:
+    invs = [dcg.DCG_INV_FP32, dcg.DCG_INV_BF16] if prec == dcg.DCG_MIXED else [dcg.DCG_INV_FP32]
+    for levels, inv in [(lv, iv) for lv in args.levels for iv in invs]:
         o = dcg.options(patch=8, overlap=2, m1=2, m2=2, max_levels=levels, precision=prec,
-                        inner_rule=dcg.DCG_INNER_FIXED, c=0.01, recurrence=dcg.DCG_FCG1)
+                        inner_rule=dcg.DCG_INNER_FIXED, c=0.01, recurrence=dcg.DCG_FCG1, ras_inverse=inv)
         try:
             dcg.dcg_setup(probs[DTS[0]], o)
         except dcg.DCGError:
@@ -212,9 +213,10 @@ def run_ours(args):
             torch.cuda.synchronize()
             t = time.perf_counter() - t0
             best = t if best is None else min(best, t)
-        tune[levels] = best
-    best_levels = min(tune, key=tune.get)
+        tune[(levels, inv)] = best
+    best_levels, best_inv = min(tune, key=tune.get)
     opts.max_levels = best_levels
+    opts.ras_inverse = best_inv
     for dt in DTS:
         dcg.dcg_setup(probs[dt], opts)
     N = probs[DTS[0]].N
@@ -367,7 +369,10 @@ def run_ours(args):
             "dtype": "f64 outer CG, f32 W-cycle" if prec == dcg.DCG_MIXED else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "mg_levels": best_levels, "mg_levels_tuning_s": {str(k): v for k, v in tune.items()},
+                       "mg_levels": best_levels,
+                       "ras_products": "tcgen05 BF16 x BF16 -> FP32" if best_inv == dcg.DCG_INV_BF16 else "FP32 SIMT",
+                       "autotune_inner_solve_s": {"levels=%d,%s" % (k[0], "bf16" if k[1] else "fp32"): v
+                                                  for k, v in tune.items()},
                        "l2": "inputs larger than L2 (BSR matrix 1.2 GB per dt)", "precision": args.precision,
                        "all_converged": ok},
             "e2e": {"value": e2e_s, "unit": "s/solve", "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": N * 8},

@@ -137,6 +137,7 @@ struct RasClass {
   int len[kMaxDim];   // box extent per axis
   int np;             // prod(len)
   int npp;            // np rounded up to a multiple of 4 (row length of the stored inverse)
+  int npk;            // np rounded up to a multiple of 16 (tensor-core N and K)
   int local_off;      // offset of the class's packed local coordinates
   int nb;             // boxes per work item (batch width of the product)
   long long inv_off;  // offset of the inverse in the level's inverse array
@@ -167,6 +168,7 @@ struct Level {
   long long ylen = 0;
   long long ras_np2 = 0;            // sum over boxes of np^2 (FMAs of one smoothing product)
   long long gmax = 0;               // max over classes of np * nb (residual tile elements)
+  bool tc = false;                  // RAS products on the tensor cores (BF16 inverses)
   void* d_inv = nullptr;            // inverses in the W-cycle precision (row-major, symmetric)
   void* d_inv_bf16 = nullptr;       // optional BF16 copy
   // vectors in the W-cycle precision

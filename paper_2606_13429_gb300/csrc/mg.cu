@@ -33,6 +33,8 @@
 #include "common.cuh"
 #include "tma.cuh"
 
+#include <cuda_bf16.h>
+
 #include <cmath>
 #include <cstdio>
 #include <map>
@@ -513,6 +515,127 @@ __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, const T* 
   }
 }
 
+// (1') Tensor-core variant (tcgen05, kind::f16): per work item of up to 128
+// boxes, D[128 boxes x npad] = G^T[128 x npad] * inv^T with BF16 operands and
+// FP32 accumulation in TMEM (the inverse is symmetric, so inv^T = inv). The
+// class inverse is stored at setup in the canonical K-major BF16 layout and
+// brought into shared memory with one bulk copy; the residual tile is
+// gathered, rounded to BF16 and written in the same layout; one thread issues
+// npad/16 MMAs (M=128, N=npad, K=16) and commits them to an mbarrier; the
+// epilogue reads TMEM with tcgen05.ld (warp w: lanes 32(w%4).., half of the
+// columns) and stores results coalesced in the work item's layout [i][128].
+template <int D>
+__global__ void __launch_bounds__(256) k_ras_solve_tc(RasArgs ra, const float* __restrict__ rvec,
+                                                       const __nv_bfloat16* __restrict__ invb, float* __restrict__ y) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar_tma;
+  __shared__ __align__(8) uint64_t bar_mma;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(&bar_tma, 1);
+    mbar_init(&bar_mma, 1);
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 256);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  unsigned ph_tma = 0, ph_mma = 0;
+  int cur_cls = -1;
+  bool failed = false;
+  const int w0 = blockIdx.x * ra.items_per_cta;
+  const int w1 = min(ra.nwork, w0 + ra.items_per_cta);
+  __nv_bfloat16* sB = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // inverse [npad][npad], canonical
+  __nv_bfloat16* sA = sB + ra.g_off;                                  // residuals [128][npad], canonical
+  for (int w = w0; w < w1; ++w) {
+    const int cls = ra.work[3 * w], first = ra.work[3 * w + 1], nb = ra.work[3 * w + 2];
+    const RasClass C = ra.classes[cls];
+    const int np = C.np, npad = C.npk;
+    __syncthreads();  // the previous item is done with sA and with TMEM
+    bool loading = false;
+    if (cls != cur_cls) {
+      if (tid == 0) {
+        const unsigned bytes = (unsigned)((size_t)npad * npad * sizeof(__nv_bfloat16));
+        mbar_expect_tx(&bar_tma, bytes);
+        tma_load_1d(sB, invb + C.inv_off, bytes, &bar_tma);
+      }
+      loading = true;
+      cur_cls = cls;
+    }
+    {
+      const int b = tid & 127;
+      int node0 = 0;
+      if (b < nb) node0 = __ldg(ra.origin + __ldg(ra.class_patches + first + b)).w;
+#pragma unroll 8
+      for (int k = tid >> 7; k < npad; k += 2) {
+        float r = 0.f;
+        if (b < nb && k < np) r = __ldg(rvec + node0 + __ldg(ra.local_off_node + C.local_off + k));
+        sA[canon_bf16(b, k, npad)] = __float2bfloat16_rn(r);
+      }
+    }
+    fence_async_smem();
+    bool ok = true;
+    if (loading) {
+      ok = mbar_wait_bounded(&bar_tma, ph_tma) || mbar_wait_bounded(&bar_tma, ph_tma);
+      ph_tma ^= 1u;
+    }
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc_fence_after();
+    if (tid == 0) {
+      const uint32_t idesc = umma_idesc_bf16(128, npad);
+      const unsigned sbo = (unsigned)(npad / 8) * 128u;
+      const unsigned a0 = smem_u32(sA), b0 = smem_u32(sB);
+      for (int k0 = 0; k0 < npad; k0 += 16) {
+        const uint64_t adesc = umma_smem_desc(a0 + (unsigned)(k0 / 8) * 128u, 128u, sbo);
+        const uint64_t bdesc = umma_smem_desc(b0 + (unsigned)(k0 / 8) * 128u, 128u, sbo);
+        umma_bf16(tmem, adesc, bdesc, idesc, k0 > 0);
+      }
+      umma_commit(&bar_mma);
+    }
+    ok = mbar_wait_bounded(&bar_mma, ph_mma) || mbar_wait_bounded(&bar_mma, ph_mma);
+    ph_mma ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc_fence_after();
+    {
+      const int quarter = warp & 3;
+      const int box = 32 * quarter + lane;
+      const int half = npad >> 1;
+      const int c0 = (warp >> 2) * half;
+      float* yi = y + ra.item_off[w];
+      for (int c = c0; c < c0 + half; c += 8) {
+        float v[8];
+        tmem_ld8(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c, v);
+        if (box < nb) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (c + j < np) yi[(size_t)(c + j) * 128 + box] = v[j];
+        }
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (failed && tid == 0) *ra.err = 1.0;
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// symmetrised inverse as BF16 in the canonical K-major layout, padded to npad
+__global__ void k_inv_bf16_canon(const double* __restrict__ a, __nv_bfloat16* __restrict__ out, int n, int npad) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)npad * npad) return;
+  const int i = (int)(t / npad), k = (int)(t % npad);
+  const double v = (i < n && k < n) ? 0.5 * (a[(long long)i * n + k] + a[(long long)k * n + i]) : 0.0;
+  out[canon_bf16(i, k, npad)] = __float2bfloat16_rn((float)v);
+}
+
 // (2) z[j] += D_j * sum over the boxes containing j of their result for j;
 // ysrc[j * 2^D + slot] is the index of that result in y (-1: no such box),
 // slot bit ax = 0 for the node's own core tile along axis ax, 1 for the
@@ -738,6 +861,7 @@ void free_level(Level& L) {
 int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
   const int D = p->dim;
   const dcg_options& o = p->opts;
+  L.tc = fp32 && o.ras_inverse == DCG_INV_BF16;  // BF16 inverses on the tensor cores
   L.tiles = Tiles1D{L.m, o.patch, o.overlap, (L.m + o.patch - 1) / o.patch};
   const int nt = L.tiles.ntile;
   L.npatch = (int)ipow(nt, D);
@@ -776,10 +900,11 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
       set_error_msg("RAS box larger than 256 nodes: reduce patch/overlap");
       return DCG_ERR_UNSUPPORTED;
     }
-    c.npp = (c.np + 3) / 4 * 4;  // rows padded: 16-byte aligned vector loads
-    c.inv_off = inv_total;       // 16-byte aligned for the bulk copy into shared memory
-    inv_total += (long long)c.np * c.npp;
-    c.nb = class_batch(c.np);
+    c.npp = (c.np + 3) / 4 * 4;    // rows padded: 16-byte aligned vector loads
+    c.npk = (c.np + 15) / 16 * 16;   // tensor-core N and K padding
+    c.inv_off = inv_total;           // 16-byte aligned for the bulk copy into shared memory
+    inv_total += L.tc ? (long long)c.npk * c.npk : (long long)c.np * c.npp;
+    c.nb = L.tc ? 128 : class_batch(c.np);
     L.npmax = std::max(L.npmax, c.np);
     L.gmax = std::max(L.gmax, (long long)c.np * c.nb);
   }
@@ -894,7 +1019,7 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
   DCG_CUDA(cudaMemcpyAsync(L.d_classes, L.classes.data(), sizeof(RasClass) * L.nclass, cudaMemcpyHostToDevice, s));
   // local inverses: box matrix from the stencil, Gauss-Jordan in FP64
   const size_t tsz = fp32 ? sizeof(float) : sizeof(double);
-  DCG_CUDA(cudaMalloc(&L.d_inv, tsz * inv_total));
+  DCG_CUDA(cudaMalloc(&L.d_inv, (L.tc ? sizeof(__nv_bfloat16) : tsz) * inv_total));
   double* work64 = nullptr;
   DCG_CUDA(cudaMalloc(&work64, sizeof(double) * (size_t)L.npmax * L.npmax));
   for (auto& c : L.classes) {
@@ -906,9 +1031,14 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
     DCG_LAUNCH_CHECK();
     k_gauss_jordan<<<1, 1024, sizeof(double) * np, s>>>(work64, np);
     DCG_LAUNCH_CHECK();
-    const int gp = (int)(((long long)np * c.npp + 255) / 256);
-    if (fp32) k_sym_convert<float><<<gp, 256, 0, s>>>(work64, (float*)L.d_inv + c.inv_off, np, c.npp);
-    else k_sym_convert<double><<<gp, 256, 0, s>>>(work64, (double*)L.d_inv + c.inv_off, np, c.npp);
+    if (L.tc) {
+      const int gp = (int)(((long long)c.npk * c.npk + 255) / 256);
+      k_inv_bf16_canon<<<gp, 256, 0, s>>>(work64, (__nv_bfloat16*)L.d_inv + c.inv_off, np, c.npk);
+    } else {
+      const int gp = (int)(((long long)np * c.npp + 255) / 256);
+      if (fp32) k_sym_convert<float><<<gp, 256, 0, s>>>(work64, (float*)L.d_inv + c.inv_off, np, c.npp);
+      else k_sym_convert<double><<<gp, 256, 0, s>>>(work64, (double*)L.d_inv + c.inv_off, np, c.npp);
+    }
     DCG_LAUNCH_CHECK();
   }
   DCG_CUDA(cudaStreamSynchronize(s));
@@ -1002,6 +1132,30 @@ int ras_step_t(dcg_problem* p, Level& L, cudaStream_t s, bool z_zero = false) {
   const double flops = 2.0 * (double)L.ras_np2;
   bytes += sizeof(T) * 2.0 * (double)L.ylen;
   int prof = prof_begin(p, PC_RAS_SOLVE, s, g_capturing);
+  if constexpr (sizeof(T) == 4) {
+    if (L.tc) {
+      long long npkmax = 0;
+      for (const auto& c : L.classes) npkmax = std::max<long long>(npkmax, c.npk);
+      RasArgs rt = ra;
+      rt.g_off = npkmax * npkmax;
+      const size_t smem_tc = sizeof(__nv_bfloat16) * (size_t)(npkmax * npkmax + 128 * npkmax);
+      const int per_sm_tc = std::max(1, std::min(2, (int)((227 * 1024) / (smem_tc + 1024))));
+      const int cap_tc = 152 * per_sm_tc;
+      rt.items_per_cta = (L.nwork + cap_tc - 1) / cap_tc;
+      const int grid_tc = (L.nwork + rt.items_per_cta - 1) / rt.items_per_cta;
+      k_ras_solve_tc<D><<<grid_tc, 256, smem_tc, s>>>(rt, (const float*)rvec, (const __nv_bfloat16*)L.d_inv,
+                                                      (float*)L.y);
+      DCG_LAUNCH_CHECK();
+      prof_end(p, prof, s, flops, bytes, g_capturing);
+      prof = prof_begin(p, PC_RAS_UPDATE, s, g_capturing);
+      k_ras_update<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(L.d_ysrc, (const T*)L.y, (T*)L.z, L.nn,
+                                                                    p->opts.ras_weights == DCG_RAS_RESTRICTED);
+      DCG_LAUNCH_CHECK();
+      prof_end(p, prof, s, (double)L.nn * (1 << D),
+               (double)L.nn * ((1 << D) * (4.0 + sizeof(T)) + 2.0 * sizeof(T)), g_capturing);
+      return DCG_OK;
+    }
+  }
   if (resident)
     k_ras_solve<T, D, true><<<grid, kRasThreads, smem, s>>>(ra, rvec, (const T*)L.d_inv, (T*)L.y);
   else
@@ -1247,6 +1401,8 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
     DCG_TRY(set_ras_smem(k_fdm_pass<double, true>));
     DCG_TRY(set_ras_smem(k_fdm_pass<double, false>));
   }
+  DCG_TRY(set_ras_smem(k_ras_solve_tc<2>));
+  DCG_TRY(set_ras_smem(k_ras_solve_tc<3>));
   DCG_TRY(set_ras_smem(k_ras_solve<float, 2, true>));
   DCG_TRY(set_ras_smem(k_ras_solve<float, 3, true>));
   DCG_TRY(set_ras_smem(k_ras_solve<float, 2, false>));

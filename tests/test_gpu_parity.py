@@ -347,3 +347,38 @@ def test_batched_matches_single():
     for k in range(4):
         assert stats[k]["true_relres"] <= 1e-8
         assert relerr(host(xs[k]), ref[k]) <= 1e-9
+
+
+# --------------------------------------------------------------------------- tensor-core RAS (BF16 inverses)
+
+
+@pytest.mark.parametrize("d,n,P,o", [(2, 32, 4, 1), (2, 64, 8, 2), (3, 12, 4, 1)])
+def test_ras_step_tensor_cores(d, n, P, o):
+    """RAS step with BF16 inverses and BF16 residuals on tcgen05 (FP32
+    accumulation): the update z_new - z matches the oracle's to BF16 rounding
+    (8 significant bits per operand)."""
+    asm, H, prob = _pair(d, n, 1e-3, mg_opts(patch=P, overlap=o), precision=dcg.DCG_MIXED)
+    dcg.dcg_setup(prob, gpu_opts(mg_opts(patch=P, overlap=o), precision=dcg.DCG_MIXED, ras_inverse=dcg.DCG_INV_BF16))
+    for k in range(2, H.J + 1):
+        nn = H.levels[k - 1].Z.shape[0]
+        f = inputs.rhs(20 + k, nn)
+        z = inputs.rhs(40 + k, nn)
+        zt = dev(z)
+        dcg.dcg_ras_step(prob, k, dev(f), zt)
+        want = H.ras_step(k, f, z) - z
+        got = host(zt) - z
+        assert relerr(got, want) <= 2e-2, (k, relerr(got, want))
+
+
+@pytest.mark.parametrize("d,n,dt", [(2, 64, 1e-5), (3, 12, 1e-4)])
+def test_dcg_tensor_cores(d, n, dt):
+    x, st, x_o, st_o, asm, f = _solve_pair(d, n, dt, mg_opts(), precision=dcg.DCG_MIXED)
+    prob = dcg.dcg_assemble(d, n, dt)
+    dcg.dcg_setup(prob, gpu_opts(mg_opts(), precision=dcg.DCG_MIXED, ras_inverse=dcg.DCG_INV_BF16))
+    xt = torch.zeros(prob.N, dtype=torch.float64, device="cuda")
+    st2 = dcg.dcg_solve(prob, dev(f), xt, tol=1e-8)
+    assert st2["status"] == dcg.DCG_OK and st2["true_relres"] <= 1e-8
+    assert abs(st2["outer_its"] - st_o.outer_its) <= 3
+    assert relerr(host(xt), x_o) <= 1e-7
+    # BF16 smoothing costs at most a few extra W-cycles per inner solve
+    assert st2["total_mg_cycles"] <= 2 * st_o.total_mg_cycles
