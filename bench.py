@@ -342,6 +342,8 @@ def run_ours(args):
         extra["dcg_all_fp64_dt1e-6"] = {"s": time.perf_counter() - t0, "outer_its": st["outer_its"], "mg_levels": fp64_levels,
                                         "total_mg_cycles": st["total_mg_cycles"], "true_relres": st["true_relres"]}
         pf.close()
+    if not args.skip_batched:
+        extra["batched"] = batched_extra(args, opts, dcg, inputs, torch)
     extra["spmv_fp64"] = {"GB_per_s": sp["bytes"] / (sp["ms"] / 1e3) / 1e9, "ms": sp["ms"] / max(1, sp["launches"])}
     extra["kernel_breakdown_warmup_ms"] = {c: round(v["ms"], 3) for c, v in breakdown.items()}
 
@@ -385,6 +387,47 @@ def run_ours(args):
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def batched_extra(args, opts, dcg, inputs, torch, nrhs=4):
+    """Independent 2D problems (n log-uniform in [64, 512], dt log-uniform in
+    [1e-6, 1e-1]), 4 right-hand sides each: one batched call against the
+    same solves one after another on one stream."""
+    plist = inputs.batched_problems(11, args.batched_problems)
+    probs, fs = [], []
+    for p, (nb, dtb) in enumerate(plist):
+        pr = dcg.dcg_assemble(2, nb, dtb)
+        dcg.dcg_setup(pr, opts)
+        probs.append(pr)
+        for r in range(nrhs):
+            fs.append(torch.from_numpy(inputs.rhs(5, pr.N, p=p, r=r)).cuda())
+    xs = [torch.zeros_like(f) for f in fs]
+    # untimed pass: builds every W-cycle graph
+    dcg.dcg_solve_batched(probs, nrhs, fs, xs, tol=1e-8, max_it=args.max_it)
+    for x in xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    code, stats = dcg.dcg_solve_batched(probs, nrhs, fs, xs, tol=1e-8, max_it=args.max_it)
+    torch.cuda.synchronize()
+    t_batched = time.perf_counter() - t0
+    for x in xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = [dcg.dcg_solve(probs[k // nrhs], fs[k], xs[k], tol=1e-8, max_it=args.max_it) for k in range(len(fs))]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    unknowns = sum(pr.N for pr in probs) * nrhs
+    out = {"problems": len(probs), "rhs_per_problem": nrhs, "unknowns_total": unknowns,
+           "n_range": [min(n for n, _ in plist), max(n for n, _ in plist)],
+           "batched_s": t_batched, "sequential_s": t_seq, "speedup": t_seq / t_batched,
+           "batched_unknowns_per_s": unknowns / t_batched,
+           "all_converged": code == dcg.DCG_OK and all(st["true_relres"] <= 1e-8 for st in stats),
+           "same_iterations_as_sequential": all(a["outer_its"] == b["outer_its"] for a, b in zip(stats, seq))}
+    for pr in probs:
+        pr.close()
+    return out
 
 
 def kernel_source_hash():
@@ -471,6 +514,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-cg", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--batched-problems", type=int, default=64)
     ap.add_argument("--levels", type=int, nargs="+", default=[2, 3, 4], help="hierarchy depths to autotune over")
     ap.add_argument("--ref-levels", type=int, default=2, help="hierarchy depth of the oracle in the reference arm")
     args = ap.parse_args()

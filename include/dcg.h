@@ -106,6 +106,12 @@ typedef struct {
   int max_restarts;  /* true-residual restarts after reconstruction [3] */
   int fcg_max_dirs;  /* FCG(inf): directions kept; 0 = up to max_it [0] */
   int check_every;   /* outer iterations between host convergence reads [1] */
+  int stall_window;  /* deflated CG: a pass whose recursive residual has not
+                        fallen below 0.9 x its best value for
+                        max(stall_window, its/4) iterations ends, is
+                        reconstructed and restarted from its true residual
+                        (such restarts do not count against max_restarts);
+                        0 = off [50] */
 } dcg_options;
 
 typedef struct {
@@ -151,13 +157,35 @@ int dcg_solve_host(dcg_problem* p, const double* f_host, double* x_host, double 
                    int max_it, dcg_stats* stats, void* stream);
 
 /* Solve nprob problems, each with nrhs right-hand sides, in one call:
- * f_dev[p*nrhs + r], x_dev[p*nrhs + r] are device arrays of problem p's N.
- * Problems may differ in n and dt; each must have been set up. The
- * right-hand sides of one problem advance together (one read of A serves
- * all of them); converged pairs drop out. stats: nprob*nrhs entries. */
+ * f_dev[p*nrhs + r], x_dev[p*nrhs + r] are device arrays of problem p's N
+ * (x in: initial guess, out: solution). Problems may differ in dim, n, dt and
+ * options; each must have been set up and may appear only once. The problems
+ * are independent, so they run concurrently: up to 16 host workers, each with
+ * its own non-blocking stream, take problems from a shared counter and solve
+ * that problem's right-hand sides in turn (every pair stops at its own
+ * convergence test). The work starts after what is already queued on
+ * `stream` and `stream` waits for all of it; the call returns when every
+ * solve has ended. stats: nprob*nrhs entries, filled per pair. Returns
+ * DCG_OK if every pair converged, else the first non-OK pair status, or the
+ * first hard error (DCG_ERR_CUDA, ...) a worker met. */
 int dcg_solve_batched(int nprob, dcg_problem* const* probs, int nrhs,
                       const double* const* f_dev, double* const* x_dev, double tol,
                       int max_it, dcg_stats* stats, void* stream);
+
+/* Choose W-cycle options for this problem by measurement. The paper fixes
+ * its options by hand (Section 5); this call is a library extension with no
+ * counterpart there. Starting from `base`, every candidate that differs in
+ * max_levels (2..4, as the mesh allows), (patch, overlap) in {(4,1), (8,1),
+ * (8,2), (12,2)} (kept when 2*overlap <= patch and the RAS box has <= 256
+ * nodes) and, in mixed precision, ras_inverse (FP32, BF16) is set up and
+ * timed: `reps` inner solves (Algorithm 3, zero start, relative tolerance
+ * inner_tol, at most base->inner_nmax cycles) of g = V^T f on `stream`.
+ * The fastest candidate wins; candidates that fail to reach inner_tol are
+ * skipped. On return the problem is set up with the winner, *best holds it
+ * and *best_ms its time per inner solve. f_dev: device array of N (a
+ * representative right-hand side). Temporary device memory: 2 n_nodes doubles. */
+int dcg_autotune(dcg_problem* p, const dcg_options* base, const double* f_dev, double inner_tol,
+                 int reps, dcg_options* best, double* best_ms, void* stream);
 
 void dcg_destroy(dcg_problem* p);
 

@@ -96,6 +96,7 @@ class FDCGOptions:
     inner_nmax: int = 100
     recurrence: str = "fcg1"       # "fcg1" | "fr" | "fcg_inf"
     max_restarts: int = 3
+    stall_window: int = 50         # restart a pass whose residual stopped falling; 0 = off
 
 
 class FDCG:
@@ -156,6 +157,10 @@ class FDCG:
         rr = r @ r
         its = 0
         conv = np.sqrt(rr) <= eps
+        # stall test: the recursive residual has not fallen below 0.9 x its
+        # best value for max(stall_window, its/4) iterations
+        stalled = False
+        best, its_best = np.sqrt(rr), 0
         while not conv and st.outer_its < max_it:
             tc = self._inner_tol(np.sqrt(rr), eps, tol)
             q = self.M_D(d, tc, st)
@@ -173,6 +178,11 @@ class FDCG:
             if np.sqrt(rr_new) <= eps:
                 conv = True
                 break
+            if np.sqrt(rr_new) < 0.9 * best:
+                best, its_best = np.sqrt(rr_new), its
+            elif o.stall_window > 0 and its - its_best > max(o.stall_window, its // 4):
+                stalled = True
+                break
             if o.recurrence == "fr":
                 d = r + (rr_new / rr) * d
             elif o.recurrence == "fcg1":
@@ -189,7 +199,7 @@ class FDCG:
                 raise ValueError(o.recurrence)
             rr = rr_new
         x = xh - self.pi(A @ xh, tc0, st) + pi_f
-        return x, conv
+        return x, conv, stalled
 
     def solve(self, f: np.ndarray, tol: float = 1e-8, max_it: int = 100000, x0=None):
         st = SolveStats()
@@ -198,13 +208,16 @@ class FDCG:
             st.converged, st.true_relres = True, 0.0
             return np.zeros_like(f), st
         eps = tol * fn
-        x, conv = self._pass(f, x0, eps, tol, max_it, st)
+        x, conv, stalled = self._pass(f, x0, eps, tol, max_it, st)
         res = f - self.A @ x
         st.true_relres = np.linalg.norm(res) / fn
-        while (st.true_relres > tol and st.restarts < self.opts.max_restarts
+        claimed = 0  # restarts after passes that reported convergence
+        while (st.true_relres > tol and (stalled or claimed < self.opts.max_restarts)
                and not st.breakdown and st.outer_its < max_it):
+            if not stalled:
+                claimed += 1
             st.restarts += 1
-            e, conv = self._pass(res, None, eps, tol, max_it, st)
+            e, conv, stalled = self._pass(res, None, eps, tol, max_it, st)
             x = x + e
             res = f - self.A @ x
             st.true_relres = np.linalg.norm(res) / fn

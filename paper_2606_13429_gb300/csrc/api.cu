@@ -6,13 +6,18 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <set>
+#include <thread>
 
 namespace dcg {
 
-long long g_launch_count = 0;
+std::atomic<long long> g_launch_count{0};
+thread_local bool t_capturing = false;
+thread_local long long t_capture_launches = 0;
 
 namespace {
 thread_local std::string g_err;
+constexpr int kBatchWorkers = 16;  // host workers (and streams) of dcg_solve_batched
 }
 
 void set_error(const char* what, cudaError_t e) {
@@ -35,7 +40,7 @@ int check_options(const dcg_options* o, int dim) {
             (o->recurrence >= 0 && o->recurrence <= 2) && (o->precision == DCG_FP64 || o->precision == DCG_MIXED) &&
             (o->ras_inverse == DCG_INV_FP32 || o->ras_inverse == DCG_INV_BF16) &&
             (o->ras_weights == 0 || o->ras_weights == 1) && (o->deflate == 0 || o->deflate == 1) &&
-            o->max_restarts >= 0 && o->fcg_max_dirs >= 0 && o->check_every >= 1;
+            o->max_restarts >= 0 && o->fcg_max_dirs >= 0 && o->check_every >= 1 && o->stall_window >= 0;
   if (!ok) {
     set_error_msg("invalid dcg_options field");
     return DCG_ERR_INVALID_ARG;
@@ -160,6 +165,7 @@ void dcg_default_options(dcg_options* o) {
   o->max_restarts = 3;
   o->fcg_max_dirs = 0;
   o->check_every = 1;
+  o->stall_window = 50;
 }
 
 const char* dcg_status_string(int s) {
@@ -319,16 +325,166 @@ int dcg_solve_host(dcg_problem* p, const double* f_host, double* x_host, double 
 
 int dcg_solve_batched(int nprob, dcg_problem* const* probs, int nrhs, const double* const* f_dev,
                       double* const* x_dev, double tol, int max_it, dcg_stats* stats, void* stream) {
-  if (nprob < 0 || nrhs < 1 || (nprob > 0 && (!probs || !f_dev || !x_dev || !stats))) return DCG_ERR_INVALID_ARG;
-  int worst = DCG_OK;
-  for (int pi = 0; pi < nprob; ++pi)
-    for (int r = 0; r < nrhs; ++r) {
-      const int k = pi * nrhs + r;
-      int st = dcg_solve(probs[pi], f_dev[k], x_dev[k], tol, max_it, &stats[k], stream);
-      if (st != DCG_OK && st != DCG_ERR_NOT_CONVERGED && st != DCG_ERR_BREAKDOWN) return st;
-      if (st != DCG_OK && worst == DCG_OK) worst = st;
+  if (nprob < 0 || nrhs < 1 || (nprob > 0 && (!probs || !f_dev || !x_dev || !stats)) || !(tol > 0) || max_it < 0) {
+    set_error_msg("dcg_solve_batched: need nprob >= 0, nrhs >= 1, arrays, tol > 0");
+    return DCG_ERR_INVALID_ARG;
+  }
+  std::set<const dcg_problem*> seen;
+  for (int i = 0; i < nprob; ++i) {
+    if (!probs[i] || !probs[i]->is_setup || !seen.insert(probs[i]).second) {
+      set_error_msg("dcg_solve_batched: every problem must be set up and appear once");
+      return probs[i] && !probs[i]->is_setup ? DCG_ERR_STATE : DCG_ERR_INVALID_ARG;
     }
+    for (int r = 0; r < nrhs; ++r)
+      if (!f_dev[i * nrhs + r] || !x_dev[i * nrhs + r]) return DCG_ERR_INVALID_ARG;
+  }
+  if (nprob == 0) return DCG_OK;
+  // Problems are independent: a pool of host workers drives them on their own
+  // non-blocking streams (each problem's right-hand sides in order), so the
+  // GPU overlaps the latency-bound kernels of different problems. Work starts
+  // after everything already queued on the caller's stream, and the caller's
+  // stream waits for every worker.
+  cudaStream_t caller = (cudaStream_t)stream;
+  int dev = 0;
+  DCG_CUDA(cudaGetDevice(&dev));
+  cudaEvent_t start = nullptr;
+  DCG_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  DCG_CUDA(cudaEventRecord(start, caller));
+  const int nworkers = nprob < kBatchWorkers ? nprob : kBatchWorkers;
+  std::atomic<int> next{0};
+  std::vector<int> wstatus(nworkers, DCG_OK);
+  std::vector<std::string> werr(nworkers);
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nworkers; ++w) {
+    pool.emplace_back([&, w]() {
+      cudaSetDevice(dev);
+      cudaStream_t ws = nullptr;
+      cudaEvent_t done = nullptr;
+      if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess ||
+          cudaStreamWaitEvent(ws, start, 0) != cudaSuccess) {
+        wstatus[w] = DCG_ERR_CUDA;
+        werr[w] = "dcg_solve_batched: worker stream setup failed";
+      } else {
+        for (;;) {
+          const int pi = next.fetch_add(1);
+          if (pi >= nprob) break;
+          for (int r = 0; r < nrhs; ++r) {
+            const int k = pi * nrhs + r;
+            const int st = solve_device(probs[pi], f_dev[k], x_dev[k], tol, max_it, &stats[k], ws);
+            if (st != DCG_OK && st != DCG_ERR_NOT_CONVERGED && st != DCG_ERR_BREAKDOWN) {
+              stats[k].status = st;
+              if (wstatus[w] == DCG_OK) {
+                wstatus[w] = st;
+                werr[w] = dcg_last_error();
+              }
+            }
+          }
+        }
+        cudaEventRecord(done, ws);
+        cudaStreamWaitEvent(caller, done, 0);
+        cudaStreamSynchronize(ws);
+      }
+      if (done) cudaEventDestroy(done);
+      if (ws) cudaStreamDestroy(ws);
+    });
+  }
+  for (auto& t : pool) t.join();
+  cudaEventDestroy(start);
+  for (int w = 0; w < nworkers; ++w)
+    if (wstatus[w] != DCG_OK) {
+      set_error_msg(werr[w]);
+      return wstatus[w];
+    }
+  int worst = DCG_OK;
+  for (int k = 0; k < nprob * nrhs; ++k)
+    if (stats[k].status != DCG_OK && worst == DCG_OK) worst = stats[k].status;
   return worst;
+}
+
+int dcg_autotune(dcg_problem* p, const dcg_options* base, const double* f_dev, double inner_tol, int reps,
+                 dcg_options* best, double* best_ms, void* stream) {
+  if (!p || !base || !f_dev || !best || !best_ms || !(inner_tol > 0) || reps < 1) {
+    set_error_msg("dcg_autotune: need problem, base, f, best, best_ms, inner_tol > 0, reps >= 1");
+    return DCG_ERR_INVALID_ARG;
+  }
+  if (!base->deflate || base->inner_rule == DCG_INNER_EXACT) {
+    set_error_msg("dcg_autotune: only W-cycle (deflated, non-exact) options have tunables");
+    return DCG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<dcg_options> cand;
+  const int tiles[4][2] = {{4, 1}, {8, 1}, {8, 2}, {12, 2}};
+  for (int lv = 2; lv <= 4; ++lv)
+    for (const auto& t : tiles)
+      for (int inv = 0; inv < (base->precision == DCG_MIXED ? 2 : 1); ++inv) {
+        dcg_options o = *base;
+        o.max_levels = lv;
+        o.patch = t[0];
+        o.overlap = t[1];
+        if (base->precision == DCG_MIXED) o.ras_inverse = inv ? DCG_INV_BF16 : DCG_INV_FP32;
+        long long box = 1;
+        for (int a = 0; a < p->dim; ++a) box *= o.patch + 2 * o.overlap;
+        if (box > 256) continue;
+        if (lv > 2 && (int)level_sizes(p->n, lv).size() < lv) continue;  // mesh allows fewer levels
+        cand.push_back(o);
+      }
+  double *g = nullptr, *z = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = DCG_OK;
+  float best_t = 0.f;
+  bool have = false;
+  auto cleanup = [&]() {
+    if (g) cudaFree(g);
+    if (z) cudaFree(z);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&g, sizeof(double) * p->n_nodes) != cudaSuccess ||
+      cudaMalloc(&z, sizeof(double) * p->n_nodes) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    cleanup();
+    set_error_msg("dcg_autotune: allocation failed");
+    return DCG_ERR_OOM;
+  }
+  for (const dcg_options& o : cand) {
+    if ((rc = dcg_setup(p, &o, stream)) != DCG_OK) {
+      if (rc == DCG_ERR_UNSUPPORTED || rc == DCG_ERR_INVALID_ARG) continue;  // candidate outside the kernels
+      break;
+    }
+    if ((rc = vec_extract(p, f_dev, g, -1, s)) != DCG_OK) break;
+    int ncyc = 0;
+    // one untimed solve builds and warms the W-cycle graph
+    if ((rc = cudaMemsetAsync(z, 0, sizeof(double) * p->n_nodes, s) == cudaSuccess ? DCG_OK : DCG_ERR_CUDA) ||
+        (rc = mg_solve(p, g, z, inner_tol, o.inner_nmax, &ncyc, s)) != DCG_OK)
+      break;
+    if (ncyc >= o.inner_nmax) continue;
+    float ms = 0.f;
+    if (cudaEventRecord(e0, s) != cudaSuccess) { rc = DCG_ERR_CUDA; break; }
+    for (int r = 0; r < reps && rc == DCG_OK; ++r) {
+      if (cudaMemsetAsync(z, 0, sizeof(double) * p->n_nodes, s) != cudaSuccess) rc = DCG_ERR_CUDA;
+      else rc = mg_solve(p, g, z, inner_tol, o.inner_nmax, &ncyc, s);
+    }
+    if (rc != DCG_OK) break;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = DCG_ERR_CUDA;
+      break;
+    }
+    if (!have || ms < best_t) {
+      best_t = ms;
+      *best = o;
+      have = true;
+    }
+  }
+  cleanup();
+  if (rc != DCG_OK) return rc;
+  if (!have) {
+    set_error_msg("dcg_autotune: no candidate reached inner_tol within inner_nmax cycles");
+    return DCG_ERR_NOT_CONVERGED;
+  }
+  *best_ms = best_t / reps;
+  return dcg_setup(p, best, stream);
 }
 
 void dcg_destroy(dcg_problem* p) {
@@ -446,6 +602,6 @@ int dcg_profile_read(dcg_problem* p, int cls, double* ms, long long* launches, d
   return DCG_OK;
 }
 
-long long dcg_kernel_launches(void) { return g_launch_count; }
+long long dcg_kernel_launches(void) { return g_launch_count.load(); }
 
 }  // extern "C"

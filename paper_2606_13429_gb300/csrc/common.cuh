@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -30,11 +31,16 @@ void set_error_msg(const std::string& msg);
 
 // Every kernel launch is followed by DCG_LAUNCH_CHECK(), which also counts it
 // (launches captured into the W-cycle graph are counted per replay instead).
-extern long long g_launch_count;
-inline void note_launches(long long n) { g_launch_count += n; }
+extern std::atomic<long long> g_launch_count;
+extern thread_local bool t_capturing;           // this thread is capturing the W-cycle graph
+extern thread_local long long t_capture_launches;
+inline void note_launches(long long n) {
+  if (t_capturing) t_capture_launches += n;
+  else g_launch_count += n;
+}
 #define DCG_LAUNCH_CHECK()                 \
   do {                                     \
-    ::dcg::g_launch_count++;               \
+    ::dcg::note_launches(1);               \
     DCG_CUDA(cudaGetLastError());          \
   } while (0)
 
@@ -218,6 +224,15 @@ struct Prof {
   long long launches[PC_COUNT] = {};
 };
 
+// Per-problem multigrid runtime state: the captured W-cycle graph and the
+// stream used to capture it.
+struct MGState {
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t wexec = nullptr;
+  bool fp32 = false;
+  long long graph_kernels = 0;  // kernel launches captured into the W-cycle graph
+};
+
 }  // namespace dcg
 
 struct dcg_problem {
@@ -244,6 +259,7 @@ struct dcg_problem {
   double* fine_f64 = nullptr;      // staging for host-array solves (N)
   double* fine_x64 = nullptr;
   dcg::Prof prof;
+  dcg::MGState mg;
 };
 
 namespace dcg {
@@ -308,6 +324,7 @@ void mg_free(dcg_problem* p);
 int mg_inner_apply(dcg_problem* p, const double* z, double* y, cudaStream_t s);
 int mg_cycles(dcg_problem* p, const double* g, double* z, int ncycles, cudaStream_t s);
 int mg_solve(dcg_problem* p, const double* g, double* z, double tol, int nmax, int* ncyc, cudaStream_t s);
+std::vector<int> level_sizes(int n, int max_levels);  // mesh sizes n_J, n_J/2, ... (finest first)
 int mg_ras_step_hook(dcg_problem* p, int level, const double* f, double* z, cudaStream_t s);
 int mg_coarse_hook(dcg_problem* p, const double* f, double* z, cudaStream_t s);
 

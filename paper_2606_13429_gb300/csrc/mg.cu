@@ -774,20 +774,17 @@ __global__ void k_from_t(const T* __restrict__ a, double* __restrict__ b, long l
 // Host side
 // ---------------------------------------------------------------------------
 
-struct MGState {
-  cudaStream_t cap = nullptr;
-  cudaGraphExec_t wexec = nullptr;
-  bool fp32 = false;
-  long long graph_kernels = 0;  // kernel launches captured into the W-cycle graph
-};
-bool g_capturing = false;  // launches are being captured into the W-cycle graph
-std::map<const dcg_problem*, MGState> g_state;
+thread_local bool g_capturing = false;  // launches are being captured into the W-cycle graph
+
+}  // namespace
 
 std::vector<int> level_sizes(int n, int max_levels) {
   std::vector<int> s{n};
   while (s.back() % 2 == 0 && s.back() >= 8 && (int)s.size() < max_levels) s.push_back(s.back() / 2);
   return s;
 }
+
+namespace {
 
 long long ipow(int b, int e) {
   long long r = 1;
@@ -1203,16 +1200,17 @@ int wcycle_dispatch(dcg_problem* p, cudaStream_t s) {
 }
 
 int build_wcycle_graph(dcg_problem* p) {
-  MGState& S = g_state[p];
+  MGState& S = p->mg;
   if (S.wexec) { cudaGraphExecDestroy(S.wexec); S.wexec = nullptr; }
   prof_clear_graph(p);
   if (!S.cap) DCG_CUDA(cudaStreamCreateWithFlags(&S.cap, cudaStreamNonBlocking));
   DCG_CUDA(cudaStreamBeginCapture(S.cap, cudaStreamCaptureModeThreadLocal));
   g_capturing = true;
-  const long long before = g_launch_count;
+  t_capturing = true;
+  t_capture_launches = 0;
   int st = S.fp32 ? wcycle_dispatch<float>(p, S.cap) : wcycle_dispatch<double>(p, S.cap);
-  S.graph_kernels = g_launch_count - before;
-  g_launch_count = before;
+  S.graph_kernels = t_capture_launches;
+  t_capturing = false;
   g_capturing = false;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(S.cap, &graph);
@@ -1225,7 +1223,7 @@ int build_wcycle_graph(dcg_problem* p) {
 }
 
 int run_wcycle(dcg_problem* p, cudaStream_t s) {
-  MGState& S = g_state[p];
+  MGState& S = p->mg;
   if (!S.wexec) DCG_TRY(build_wcycle_graph(p));
   DCG_CUDA(cudaGraphLaunch(S.wexec, s));
   note_launches(S.graph_kernels);
@@ -1242,12 +1240,9 @@ void mg_free(dcg_problem* p) {
   cudaFree(p->coarse.S64); cudaFree(p->coarse.S32); cudaFree(p->coarse.lam64); cudaFree(p->coarse.lam32);
   cudaFree(p->coarse.tmp);
   p->coarse = Coarse{};
-  auto it = g_state.find(p);
-  if (it != g_state.end()) {
-    if (it->second.wexec) cudaGraphExecDestroy(it->second.wexec);
-    if (it->second.cap) cudaStreamDestroy(it->second.cap);
-    g_state.erase(it);
-  }
+  if (p->mg.wexec) cudaGraphExecDestroy(p->mg.wexec);
+  if (p->mg.cap) cudaStreamDestroy(p->mg.cap);
+  p->mg = MGState{};
 }
 
 int mg_setup(dcg_problem* p, cudaStream_t s) {
@@ -1359,7 +1354,7 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
   }
   // --- buffers and RAS
   const size_t tsz = fp32 ? sizeof(float) : sizeof(double);
-  g_state[p].fp32 = fp32;
+  p->mg.fp32 = fp32;
   for (int k = 0; k < J; ++k) {
     Level& L = p->levels[k];
     DCG_CUDA(cudaMalloc(&L.f, tsz * L.nn));
@@ -1472,7 +1467,7 @@ int exact_solve(dcg_problem* p, const double* g, double* z, cudaStream_t s) {
 int mg_cycles(dcg_problem* p, const double* g, double* z, int ncycles, cudaStream_t s) {
   if (p->levels.empty()) return DCG_ERR_STATE;
   if (exact_mode(p)) return exact_solve(p, g, z, s);
-  const bool fp32 = g_state[p].fp32;
+  const bool fp32 = p->mg.fp32;
   for (int c = 0; c < ncycles; ++c) {
     DCG_TRY(fp32 ? inner_residual<float>(p, g, z, s) : inner_residual<double>(p, g, z, s));
     DCG_TRY(run_wcycle(p, s));
@@ -1490,7 +1485,7 @@ int mg_solve(dcg_problem* p, const double* g, double* z, double tol, int nmax, i
   if (p->levels.empty()) return DCG_ERR_STATE;
   *ncyc = 0;
   if (exact_mode(p)) return exact_solve(p, g, z, s);
-  const bool fp32 = g_state[p].fp32;
+  const bool fp32 = p->mg.fp32;
   int n = 0;
   for (;;) {
     DCG_TRY(fp32 ? inner_residual<float>(p, g, z, s) : inner_residual<double>(p, g, z, s));
@@ -1511,7 +1506,7 @@ int mg_solve(dcg_problem* p, const double* g, double* z, double tol, int nmax, i
 int mg_ras_step_hook(dcg_problem* p, int level, const double* f, double* z, cudaStream_t s) {
   if (level < 2 || level > (int)p->levels.size()) return DCG_ERR_INVALID_ARG;
   Level& L = p->levels[level - 1];
-  const bool fp32 = g_state[p].fp32;
+  const bool fp32 = p->mg.fp32;
   const int g = grid_for(L.nn, 256, 8192);
   if (fp32) {
     k_to_t<float><<<g, 256, 0, s>>>(f, (float*)L.f, L.nn);
@@ -1531,7 +1526,7 @@ int mg_ras_step_hook(dcg_problem* p, int level, const double* f, double* z, cuda
 int mg_coarse_hook(dcg_problem* p, const double* f, double* z, cudaStream_t s) {
   if (p->levels.empty()) return DCG_ERR_STATE;
   Level& L = p->levels[0];
-  const bool fp32 = g_state[p].fp32;
+  const bool fp32 = p->mg.fp32;
   const int g = grid_for(L.nn, 256, 8192);
   if (fp32) {
     k_to_t<float><<<g, 256, 0, s>>>(f, (float*)L.f, L.nn);

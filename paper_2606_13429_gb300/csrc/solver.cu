@@ -147,7 +147,12 @@ int pi_of_Ax(Ctx& c, const double* x, double* z, double tc, bool in_iter) {
 }
 
 // one FDCG pass: solve A x = f, x0 from x (if use_x0), result into x
-int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged) {
+// One pass of Algorithm 2 from x0 (or zero). *stalled is set when the pass
+// ended because its recursive residual stopped falling (no value below 0.9 x
+// the best one for max(stall_window, its/4) iterations): the recursion of an
+// inexactly projected operator can lose orthogonality at large dt, and the
+// caller then restarts from the true residual of the reconstructed iterate.
+int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged, bool* stalled) {
   dcg_problem* p = c.p;
   SolverBuffers& b = p->sb;
   cudaStream_t s = c.s;
@@ -183,6 +188,10 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged) 
   if (std::sqrt(rr) <= c.eps) *converged = true;
   const bool fcginf = c.rule == R_FCGINF;
   int ndir = 0;
+  *stalled = false;
+  const int window = p->opts.stall_window;
+  double best = std::sqrt(rr);
+  int its = 0, its_best = 0;
   while (!*converged && c.st->outer_its < c.max_it) {
     const double rnorm = std::sqrt(rr);
     const double tc = inner_tol(c, rnorm);
@@ -212,6 +221,14 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged) 
     }
     if (std::sqrt(rrn) <= c.eps) {
       *converged = true;
+      break;
+    }
+    ++its;
+    if (std::sqrt(rrn) < 0.9 * best) {
+      best = std::sqrt(rrn);
+      its_best = its;
+    } else if (window > 0 && its - its_best > std::max(window, its / 4)) {
+      *stalled = true;
       break;
     }
     if (fcginf) {
@@ -323,23 +340,26 @@ int solve_device(dcg_problem* p, const double* f, double* x, double tol, int max
     return DCG_OK;
   }
   c.eps = tol * c.fnorm;
+  bool stalled = false;
   if (!o.deflate) {
     DCG_TRY(plain_cg(c, f, x));
   } else {
     if (c.rule == R_FCGINF && !b.dirs) return DCG_ERR_STATE;
     bool conv = false;
-    DCG_TRY(fdcg_pass(c, f, x, x0_nonzero, &conv));
+    DCG_TRY(fdcg_pass(c, f, x, x0_nonzero, &conv, &stalled));
   }
   // true residual
   DCG_TRY(spmv_residual(p, f, x, b.u, S_TMP0, s));
   DCG_TRY(read_scalars(p, s));
   st->true_relres = std::sqrt(p->scal_host[S_TMP0]) / c.fnorm;
   if (o.deflate) {
-    while (st->true_relres > tol && st->restarts < o.max_restarts && st->status == DCG_OK &&
+    int claimed = 0;  // restarts after passes that reported convergence
+    while (st->true_relres > tol && (stalled || claimed < o.max_restarts) && st->status == DCG_OK &&
            st->outer_its < max_it) {
+      if (!stalled) ++claimed;
       st->restarts++;
       bool conv = false;
-      DCG_TRY(fdcg_pass(c, b.u, b.e, false, &conv));
+      DCG_TRY(fdcg_pass(c, b.u, b.e, false, &conv, &stalled));
       k_axpy<<<grid_n(N), kRedThreads, 0, s>>>(x, b.e, N);
       DCG_LAUNCH_CHECK();
       DCG_TRY(spmv_residual(p, f, x, b.u, S_TMP0, s));

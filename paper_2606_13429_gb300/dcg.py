@@ -42,7 +42,8 @@ class dcg_options(C.Structure):
                 ("m2", C.c_int), ("inner_rule", C.c_int), ("c", C.c_double), ("inner_nmax", C.c_int),
                 ("recurrence", C.c_int), ("precision", C.c_int), ("ras_inverse", C.c_int),
                 ("ras_weights", C.c_int), ("deflate", C.c_int), ("max_restarts", C.c_int),
-                ("fcg_max_dirs", C.c_int), ("check_every", C.c_int)]
+                ("fcg_max_dirs", C.c_int), ("check_every", C.c_int),
+                ("stall_window", C.c_int)]
 
 
 class dcg_stats(C.Structure):
@@ -97,6 +98,7 @@ def load(path: str = LIB_PATH):
         "dcg_profile_read": (I, [P, I, C.POINTER(D), C.POINTER(LL), C.POINTER(D), C.POINTER(D), VP]),
         "dcg_kernel_launches": (LL, []),
         "dcg_coarse_solve_static": (I, [P, VP, VP, VP]),
+        "dcg_autotune": (I, [P, C.POINTER(dcg_options), VP, D, I, C.POINTER(dcg_options), C.POINTER(D), VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -252,6 +254,17 @@ def dcg_solve_batched(probs, nrhs, fs, xs, tol=1e-8, max_it=100000, stream=None)
     code = load().dcg_solve_batched(len(probs), P, nrhs, F, X, tol, max_it, stats, _stream(stream))
     _check(code, "dcg_solve_batched", ok=(DCG_OK, DCG_ERR_NOT_CONVERGED, DCG_ERR_BREAKDOWN))
     return code, [s.as_dict() for s in stats]
+
+
+def dcg_autotune(prob: Problem, f, base: dcg_options | None = None, inner_tol=1e-6, reps=3, stream=None, **kw):
+    """Measure the W-cycle candidates on right-hand side f; the problem is left
+    set up with the fastest. Returns (options, ms per inner solve)."""
+    b = base if base is not None else options(**kw)
+    best, ms = dcg_options(), C.c_double()
+    _check(load().dcg_autotune(prob.ptr, C.byref(b), _dptr(f, prob.N, "f"), inner_tol, reps, C.byref(best),
+                               C.byref(ms), _stream(stream)), "dcg_autotune")
+    prob.opts = best
+    return best, ms.value
 
 
 def dcg_export_pattern(prob: Problem):

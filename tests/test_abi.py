@@ -38,7 +38,7 @@ def test_default_options(lib):
     assert (o.max_levels, o.patch, o.overlap, o.m1, o.m2) == (4, 4, 1, 2, 2)
     assert o.inner_rule == dcg.DCG_INNER_FIXED and abs(o.c - 0.01) < 1e-15
     assert o.recurrence == dcg.DCG_FCG1 and o.precision == dcg.DCG_FP64 and o.deflate == 1
-    assert o.inner_nmax == 100 and o.max_restarts == 3 and o.check_every == 1
+    assert o.inner_nmax == 100 and o.max_restarts == 3 and o.check_every == 1 and o.stall_window == 50
 
 
 def test_status_strings(lib):
@@ -72,3 +72,17 @@ def test_binding_is_marshalling_only():
         if fn.endswith(".py"):
             src = open(os.path.join(pkg, fn)).read()
             assert not re.search(r"^\s*(from|import)\s+oracle", src, re.M), fn
+
+
+def test_batched_and_autotune_reject_bad_arguments_without_gpu(lib):
+    st = (dcg.dcg_stats * 1)()
+    assert lib.dcg_solve_batched(-1, None, 1, None, None, 1e-8, 10, st, None) == dcg.DCG_ERR_INVALID_ARG
+    assert lib.dcg_solve_batched(1, None, 1, None, None, 1e-8, 10, st, None) == dcg.DCG_ERR_INVALID_ARG
+    assert lib.dcg_solve_batched(0, None, 0, None, None, 1e-8, 10, st, None) == dcg.DCG_ERR_INVALID_ARG
+    # an empty batch is a no-op that touches no device
+    assert lib.dcg_solve_batched(0, None, 1, None, None, 1e-8, 10, st, None) == dcg.DCG_OK
+    best, ms = dcg.dcg_options(), C.c_double()
+    base = dcg.options()
+    assert lib.dcg_autotune(None, C.byref(base), None, 1e-6, 3, C.byref(best), C.byref(ms), None) == \
+        dcg.DCG_ERR_INVALID_ARG
+    assert "dcg_autotune" in dcg.last_error()

@@ -265,6 +265,29 @@ def test_dcg_recurrences(rec):
     assert relerr(x, x_o) <= 1e-7
 
 
+@pytest.mark.parametrize("window", [0, 50])
+def test_dcg_stall_restart(window):
+    """Loose inner tolerance at dt = 0.1: without the stall restart both the
+    GPU solver and the oracle stagnate; with it both reach 1e-8 after
+    restarting from the true residual."""
+    o = mg_opts(patch=4, overlap=1, max_levels=2)
+    asm = fem.assemble(2, 24, 0.1)
+    f = inputs.rhs(5, asm.mesh.n_unknowns)
+    prob = dcg.dcg_assemble(2, 24, 0.1)
+    dcg.dcg_setup(prob, gpu_opts(o, c=50.0, stall_window=window))
+    x = torch.zeros(prob.N, dtype=torch.float64, device="cuda")
+    st = dcg.dcg_solve(prob, dev(f), x, tol=1e-8, max_it=1500)
+    x_o, st_o = solvers.FDCG(asm, solvers.FDCGOptions(mg=o, c=50.0, stall_window=window)).solve(f, max_it=1500)
+    if window == 0:
+        assert st["status"] == dcg.DCG_ERR_NOT_CONVERGED and st["true_relres"] > 1e-6
+        assert not st_o.converged
+    else:
+        assert st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8 and st["restarts"] >= 1
+        assert st_o.converged
+        assert abs(st["outer_its"] - st_o.outer_its) <= max(2, 0.25 * st_o.outer_its)
+        assert relerr(host(x), x_o) <= 1e-7
+
+
 @pytest.mark.parametrize("d,n,dt", [(2, 32, 1e-3), (2, 64, 1e-5), (3, 8, 1e-4)])
 def test_dcg_mixed(d, n, dt):
     x, st, x_o, st_o, asm, f = _solve_pair(d, n, dt, mg_opts(), precision=dcg.DCG_MIXED)
@@ -347,6 +370,111 @@ def test_batched_matches_single():
     for k in range(4):
         assert stats[k]["true_relres"] <= 1e-8
         assert relerr(host(xs[k]), ref[k]) <= 1e-9
+
+
+def _uneven_batch(nprob=20, nrhs=3):
+    """Problems of both dimensions, several sizes, time steps and precisions
+    (more problems than the library's 16 batch workers)."""
+    probs, fs = [], []
+    for p in range(nprob):
+        d = 3 if p % 5 == 4 else 2
+        n = [16, 24, 32, 40][p % 4] if d == 2 else [8, 12][p % 2]
+        dt = [1e-6, 1e-4, 1e-2][p % 3]
+        prob = dcg.dcg_assemble(d, n, dt)
+        dcg.dcg_setup(prob, dcg.options(precision=dcg.DCG_MIXED if p % 2 else dcg.DCG_FP64))
+        probs.append(prob)
+        for r in range(nrhs):
+            fs.append(dev(inputs.rhs(7, prob.N, p=p, r=r)))
+    return probs, fs
+
+
+def test_batched_uneven_equals_sequential_bitwise():
+    """Concurrent batched solves give the same bits as one-at-a-time solves:
+    every reduction is deterministic and independent of the stream."""
+    nrhs = 3
+    probs, fs = _uneven_batch(20, nrhs)
+    seq, seq_stats = [], []
+    for k, f in enumerate(fs):
+        x = torch.zeros_like(f)
+        seq_stats.append(dcg.dcg_solve(probs[k // nrhs], f, x))
+        seq.append(host(x))
+    xs = [torch.zeros_like(f) for f in fs]
+    code, stats = dcg.dcg_solve_batched(probs, nrhs, fs, xs)
+    assert code == dcg.DCG_OK
+    for k in range(len(fs)):
+        assert stats[k]["status"] == dcg.DCG_OK
+        assert stats[k]["true_relres"] <= 1e-8
+        assert stats[k]["outer_its"] == seq_stats[k]["outer_its"]
+        assert stats[k]["total_mg_cycles"] == seq_stats[k]["total_mg_cycles"]
+        assert np.array_equal(host(xs[k]), seq[k])
+
+
+def test_batched_orders_against_caller_stream():
+    """Work queued on the caller's stream before the call is seen by the
+    batch, and work queued after it sees the solutions."""
+    probs, fs = _uneven_batch(4, 2)
+    ref = []
+    for k, f in enumerate(fs):
+        x = torch.zeros_like(f)
+        dcg.dcg_solve(probs[k // 2], f, x)
+        ref.append(host(x))
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        big = torch.empty(1 << 26, dtype=torch.float64, device="cuda")
+        big.normal_()  # a long kernel ahead of the inputs on s
+        f2 = [f * 1.0 + 0.0 * big[: f.numel()] for f in fs]
+        xs = [torch.zeros_like(f) for f in fs]
+        code, _ = dcg.dcg_solve_batched(probs, 2, f2, xs, stream=s.cuda_stream)
+        out = [x.clone() for x in xs]
+    s.synchronize()
+    assert code == dcg.DCG_OK
+    for k in range(len(fs)):
+        assert np.array_equal(out[k].cpu().numpy(), ref[k])
+
+
+def test_batched_not_converged_reports_per_pair():
+    probs, fs = _uneven_batch(3, 2)
+    xs = [torch.zeros_like(f) for f in fs]
+    code, stats = dcg.dcg_solve_batched(probs, 2, fs, xs, max_it=1)
+    assert code == dcg.DCG_ERR_NOT_CONVERGED
+    assert all(st["status"] == dcg.DCG_ERR_NOT_CONVERGED for st in stats)
+    assert all(st["true_relres"] > 1e-8 for st in stats)
+
+
+def test_batched_rejects_duplicates_and_unset_problems():
+    prob = dcg.dcg_assemble(2, 16, 1e-3)
+    f = dev(inputs.rhs(0, prob.N))
+    x1, x2 = torch.zeros_like(f), torch.zeros_like(f)
+    with pytest.raises(dcg.DCGError):
+        dcg.dcg_solve_batched([prob], 1, [f], [x1])  # not set up
+    dcg.dcg_setup(prob, dcg.options())
+    with pytest.raises(dcg.DCGError):
+        dcg.dcg_solve_batched([prob, prob], 1, [f, f], [x1, x2])
+
+
+@pytest.mark.parametrize("d,n,prec", [(2, 64, dcg.DCG_MIXED), (2, 48, dcg.DCG_FP64), (3, 16, dcg.DCG_FP64)])
+def test_autotune_picks_a_valid_candidate(d, n, prec):
+    prob = dcg.dcg_assemble(d, n, 1e-4)
+    f = dev(inputs.rhs(3, prob.N))
+    best, ms = dcg.dcg_autotune(prob, f, dcg.options(precision=prec), inner_tol=1e-6, reps=2)
+    assert ms > 0
+    assert best.precision == prec
+    assert (best.patch, best.overlap) in [(4, 1), (8, 1), (8, 2), (12, 2)]
+    assert (best.patch + 2 * best.overlap) ** d <= 256
+    assert 2 <= best.max_levels <= 4
+    if prec == dcg.DCG_FP64:
+        assert best.ras_inverse == dcg.DCG_INV_FP32
+    # the problem is left set up with the winner, and it solves
+    assert prob.levels == len(mg.level_sizes(n, best.max_levels))
+    x = torch.zeros_like(f)
+    st = dcg.dcg_solve(prob, f, x)
+    assert st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8
+    x_ref = torch.zeros_like(f)
+    prob2 = dcg.dcg_assemble(d, n, 1e-4)
+    dcg.dcg_setup(prob2, best)
+    dcg.dcg_solve(prob2, f, x_ref)
+    assert np.array_equal(host(x), host(x_ref))
 
 
 # --------------------------------------------------------------------------- tensor-core RAS (BF16 inverses)

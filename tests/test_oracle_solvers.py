@@ -157,3 +157,18 @@ def test_max_it_cap_reports_not_converged():
     assert st.outer_its == 3 and not st.converged
     x, st = solvers.plain_cg(asm.matrix(), f, tol=1e-12, max_it=3)
     assert st.outer_its == 3 and not st.converged
+
+
+def test_stall_restart_recovers_from_stagnation():
+    """A very loose inner tolerance (c_F = 50) perturbs the deflated operator
+    enough that the FCG(1) recursion stops reducing its residual at large dt;
+    without the stall restart the solve stagnates far above 1e-8, with it the
+    restarted passes reach the tolerance."""
+    asm = fem.assemble(2, 24, 0.1)
+    f = inputs.rhs(5, asm.mesh.n_unknowns)
+    o = mg.MGOptions(patch=4, overlap=1, max_levels=2)
+    _, st0 = solvers.FDCG(asm, solvers.FDCGOptions(mg=o, c=50.0, stall_window=0)).solve(f, max_it=1500)
+    assert not st0.converged and st0.true_relres > 1e-6 and st0.outer_its == 1500
+    x, st = solvers.FDCG(asm, solvers.FDCGOptions(mg=o, c=50.0, stall_window=50)).solve(f, max_it=1500)
+    assert st.converged and st.true_relres <= 1e-8 and st.restarts >= 1 and st.outer_its < 500
+    assert np.linalg.norm(f - asm.matrix() @ x) <= 1e-8 * np.linalg.norm(f)
