@@ -389,10 +389,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def batched_extra(args, opts, dcg, inputs, torch, nrhs=4):
+def batched_extra(args, opts, dcg, inputs, torch):
     """Independent 2D problems (n log-uniform in [64, 512], dt log-uniform in
     [1e-6, 1e-1]), 4 right-hand sides each: one batched call against the
     same solves one after another on one stream."""
+    nrhs = args.batched_rhs
     plist = inputs.batched_problems(11, args.batched_problems)
     probs, fs = [], []
     for p, (nb, dtb) in enumerate(plist):
@@ -402,8 +403,8 @@ def batched_extra(args, opts, dcg, inputs, torch, nrhs=4):
         for r in range(nrhs):
             fs.append(torch.from_numpy(inputs.rhs(5, pr.N, p=p, r=r)).cuda())
     xs = [torch.zeros_like(f) for f in fs]
-    # untimed pass: builds every W-cycle graph
-    dcg.dcg_solve_batched(probs, nrhs, fs, xs, tol=1e-8, max_it=args.max_it)
+    # one outer iteration per problem, untimed: builds every W-cycle graph
+    dcg.dcg_solve_batched(probs, 1, fs[::nrhs], xs[::nrhs], tol=1e-8, max_it=1)
     for x in xs:
         x.zero_()
     torch.cuda.synchronize()
@@ -516,6 +517,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--batched-problems", type=int, default=64)
+    ap.add_argument("--batched-rhs", type=int, default=4)
     ap.add_argument("--levels", type=int, nargs="+", default=[2, 3, 4], help="hierarchy depths to autotune over")
     ap.add_argument("--ref-levels", type=int, default=2, help="hierarchy depth of the oracle in the reference arm")
     args = ap.parse_args()

@@ -670,71 +670,138 @@ __global__ void k_ras_update(const int* __restrict__ ysrc, const T* __restrict__
   }
 }
 
-// padded panel row length of the coarse passes: odd, so rows start in
-// different shared-memory banks
-__host__ __device__ inline int fdm_row(int m) { return (m % 2 == 1) ? m + 2 : m + 1; }
+// Four consecutive shared-memory values (16-byte aligned) into registers.
+__device__ __forceinline__ void lds4(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double (&v)[4]) {
+  const double2 t0 = *reinterpret_cast<const double2*>(p);
+  const double2 t1 = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+}
 
-// Coarsest solve pass: out = S applied along one axis, as the GEMM
-// C[i][n] = sum_j S[i][j] B[j][n] with B[j][n] = in[(n / inner) m inner + j inner + n % inner]
-// (inner = m^axis). A CTA owns a 32x32 tile of C; the whole 32 x m panel of
-// S and m x 32 panel of B are staged in shared memory in one load round
-// (for axis 0, B's columns are contiguous in memory and the panel is stored
-// transposed), then 256 threads compute 4 outputs each; optional division by
-// the eigenvalues in the epilogue.
+// Coarsest solve pass: S applied along one axis of the level grid, as the GEMM
+//   C[i][n] = sum_k S[k][i] B[k][n],  B[k][n] = in[(n / inner) m inner + k inner + n % inner]
+// (inner = m^axis; S is symmetric, so S[k][i] = S[i][k]), with optional
+// division by the eigenvalues in the epilogue. A CTA of 64 threads owns a
+// 32 x 32 tile of C, each thread a 4 x 4 register block; k runs through
+// chunks of 32 staged in two shared-memory buffers, the next chunk held in
+// registers while the current one is multiplied. The k sum runs in order
+// 0..m-1 for every output. Rows of S and columns of B are read coalesced (for
+// axis 0 a warp reads 32 consecutive k of one column and stores them
+// transposed).
+constexpr int kFdmTile = 32, kFdmLd = 36;
+
 template <typename T, bool AXIS0>
-__global__ void __launch_bounds__(256) k_fdm_pass(const T* __restrict__ in, T* __restrict__ out,
-                                                   const T* __restrict__ S, const T* __restrict__ lam, int m,
-                                                   long long inner, long long ncols) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int mp = fdm_row(m);                              // odd padded row length: no bank conflicts
-  T* sS = reinterpret_cast<T*>(smem_raw);                 // [32][mp]
-  T* sB = sS + 32 * mp;                                   // AXIS0: [32][mp] (n-major), else [m][32]
-  const int tid = threadIdx.x;
-  const int i0 = blockIdx.y * 32;
-  const unsigned n0 = blockIdx.x * 32u;
-  const unsigned ui = (unsigned)inner;
-  // one load round: rows r = 0..31 of the S panel (and of the transposed B
-  // panel for axis 0), columns j = tid, tid+256, ... (no division)
-  for (int j = tid; j < m; j += 256) {
-#pragma unroll 8
-    for (int r = 0; r < 32; ++r) {
-      const int ii = i0 + r;
-      sS[r * mp + j] = ii < m ? __ldg(S + (size_t)ii * m + j) : (T)0;
+__global__ void __launch_bounds__(64) k_fdm_pass(const T* __restrict__ in, T* __restrict__ out,
+                                                  const T* __restrict__ S, const T* __restrict__ lam, int m,
+                                                  long long inner, long long ncols) {
+  constexpr int KC = kFdmTile, LD = kFdmLd, R = KC * kFdmTile / 64;
+  __shared__ __align__(16) T sA[2][KC][LD];
+  __shared__ __align__(16) T sB[2][KC][LD];
+  const int tid = threadIdx.x, lane = tid & 31, half = tid >> 5;
+  const int i0 = blockIdx.y * kFdmTile;
+  const long long n0 = (long long)blockIdx.x * kFdmTile;
+  const bool ia_ok = i0 + lane < m;
+  // column of B this thread loads (all chunks) when the columns are the fast index
+  const long long nb_l = n0 + lane;
+  const bool nb_ok = nb_l < ncols;
+  long long bbase = 0;
+  if (!AXIS0 && nb_ok) {
+    const long long hi = nb_l / inner;
+    bbase = hi * m * inner + (nb_l - hi * inner);
+  }
+  T ra[R], rb[R];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k = half + 2 * r;  // row of the chunk
+      const int kk = k0 + k;
+      ra[r] = (kk < m && ia_ok) ? __ldg(S + (size_t)kk * m + i0 + lane) : (T)0;
       if (AXIS0) {
-        const unsigned nb = n0 + r;
-        sB[r * mp + j] = nb < (unsigned)ncols ? __ldg(in + (size_t)nb * m + j) : (T)0;
+        const long long nb = n0 + k;  // here r walks the columns, lane the k
+        const int kb = k0 + lane;
+        rb[r] = (nb < ncols && kb < m) ? __ldg(in + (size_t)nb * m + kb) : (T)0;
+      } else {
+        rb[r] = (kk < m && nb_ok) ? __ldg(in + bbase + (size_t)kk * inner) : (T)0;
       }
     }
-  }
-  if (!AXIS0) {
-    const int c = tid & 31;
-    const unsigned nb = n0 + c;
-    const bool okc = nb < (unsigned)ncols;
-    const unsigned hi = okc ? nb / ui : 0u;
-    const size_t base = (size_t)hi * m * ui + (nb - hi * ui);
-#pragma unroll 8
-    for (int j = tid >> 5; j < m; j += 8) sB[j * 32 + c] = okc ? __ldg(in + base + (size_t)j * ui) : (T)0;
-  }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k = half + 2 * r;
+      sA[buf][k][lane] = ra[r];
+      if (AXIS0) sB[buf][lane][k] = rb[r];
+      else sB[buf][k][lane] = rb[r];
+    }
+  };
+  const int ti = (tid >> 3) * 4, tn = (tid & 7) * 4;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q] = (T)0;
+  const int nchunks = (m + KC - 1) / KC;
+  load(0);
+  store(0);
   __syncthreads();
-  const int ti = tid >> 3, tn = (tid & 7) * 4;
-  T acc[4] = {0, 0, 0, 0};
-  const T* srow = sS + ti * mp;
-#pragma unroll 4
-  for (int k = 0; k < m; ++k) {
-    const T sv = srow[k];
+  for (int c = 0; c < nchunks; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < nchunks) load((c + 1) * KC);
+#pragma unroll 8
+    for (int k = 0; k < KC; ++k) {
+      T av[4], bv[4];
+      lds4(&sA[buf][k][ti], av);
+      lds4(&sB[buf][k][tn], bv);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += sv * (AXIS0 ? sB[(tn + q) * mp + k] : sB[k * 32 + tn + q]);
-  }
-  const int ii = i0 + ti;
-  if (ii >= m) return;
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const unsigned nb = n0 + tn + q;
-    if (nb >= (unsigned)ncols) continue;
-    const unsigned hi = nb / ui;
-    const long long o = (long long)hi * m * ui + (long long)ii * ui + (nb - hi * ui);
-    out[o] = lam ? acc[q] / lam[o] : acc[q];
+        for (int q = 0; q < 4; ++q) acc[a][q] = fma(av[a], bv[q], acc[a][q]);
+    }
+    if (c + 1 < nchunks) store(buf ^ 1);
+    __syncthreads();
   }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int ii = i0 + ti + a;
+    if (ii >= m) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long nb = n0 + tn + q;
+      if (nb >= ncols) continue;
+      const long long hi = nb / inner;
+      const long long o = hi * m * inner + (long long)ii * inner + (nb - hi * inner);
+      out[o] = lam ? acc[a][q] / lam[o] : acc[a][q];
+    }
+  }
+}
+
+// z = S^(x)D Lambda^-1 S^(x)D f on the coarsest grid: 2D passes along
+// axes 0, 1 (with Lambda^-1), 1, 0; 3D along 0, 1, 2 (Lambda^-1), 2, 1, 0.
+// tmp: scratch of m^D values. Returns the number of kernels launched.
+template <typename T, int D>
+int fdm_passes(const T* f, T* z, T* tmp, const T* S, const T* lam, int m, cudaStream_t s) {
+  long long nn = 1;
+  for (int k = 0; k < D; ++k) nn *= m;
+  const long long ncols = nn / m;
+  const dim3 grid((unsigned)((ncols + kFdmTile - 1) / kFdmTile), (unsigned)((m + kFdmTile - 1) / kFdmTile));
+  const long long in1 = 1, inm = m, inmm = (long long)m * m;
+  if (D == 2) {
+    k_fdm_pass<T, true><<<grid, 64, 0, s>>>(f, tmp, S, nullptr, m, in1, ncols);
+    k_fdm_pass<T, false><<<grid, 64, 0, s>>>(tmp, z, S, lam, m, inm, ncols);
+    k_fdm_pass<T, false><<<grid, 64, 0, s>>>(z, tmp, S, nullptr, m, inm, ncols);
+    k_fdm_pass<T, true><<<grid, 64, 0, s>>>(tmp, z, S, nullptr, m, in1, ncols);
+  } else {
+    k_fdm_pass<T, true><<<grid, 64, 0, s>>>(f, tmp, S, nullptr, m, in1, ncols);
+    k_fdm_pass<T, false><<<grid, 64, 0, s>>>(tmp, z, S, nullptr, m, inm, ncols);
+    k_fdm_pass<T, false><<<grid, 64, 0, s>>>(z, tmp, S, lam, m, inmm, ncols);
+    k_fdm_pass<T, false><<<grid, 64, 0, s>>>(tmp, z, S, nullptr, m, inmm, ncols);
+    k_fdm_pass<T, false><<<grid, 64, 0, s>>>(z, tmp, S, nullptr, m, inm, ncols);
+    k_fdm_pass<T, true><<<grid, 64, 0, s>>>(tmp, z, S, nullptr, m, in1, ncols);
+  }
+  return 2 * D;
 }
 
 // FP64 fine residual r = g - Z_J z, stored into the cycle's level-J RHS (in
@@ -1070,27 +1137,8 @@ int coarse_solve_t(dcg_problem* p, const T* f, T* z, cudaStream_t s) {
   const Coarse& C = p->coarse;
   const long long nn = ipow(C.m, D);
   const int prof = prof_begin(p, PC_COARSE, s, g_capturing);
-  T* tmp = (T*)C.tmp;
-  const T* S = coarse_S<T>(C);
-  const T* lam = coarse_lam<T>(C);
-  const long long ncols = nn / C.m;
-  const dim3 grid((unsigned)((ncols + 31) / 32), (unsigned)((C.m + 31) / 32));
-  const size_t smem = sizeof(T) * 2 * 32 * (size_t)fdm_row(C.m);
-  const long long in1 = 1, inm = C.m, inmm = (long long)C.m * C.m;
-  if (D == 2) {
-    k_fdm_pass<T, true><<<grid, 256, smem, s>>>(f, tmp, S, nullptr, C.m, in1, ncols);
-    k_fdm_pass<T, false><<<grid, 256, smem, s>>>(tmp, z, S, lam, C.m, inm, ncols);
-    k_fdm_pass<T, false><<<grid, 256, smem, s>>>(z, tmp, S, nullptr, C.m, inm, ncols);
-    k_fdm_pass<T, true><<<grid, 256, smem, s>>>(tmp, z, S, nullptr, C.m, in1, ncols);
-  } else {
-    k_fdm_pass<T, true><<<grid, 256, smem, s>>>(f, tmp, S, nullptr, C.m, in1, ncols);
-    k_fdm_pass<T, false><<<grid, 256, smem, s>>>(tmp, z, S, nullptr, C.m, inm, ncols);
-    k_fdm_pass<T, false><<<grid, 256, smem, s>>>(z, tmp, S, lam, C.m, inmm, ncols);
-    k_fdm_pass<T, false><<<grid, 256, smem, s>>>(tmp, z, S, nullptr, C.m, inmm, ncols);
-    k_fdm_pass<T, false><<<grid, 256, smem, s>>>(z, tmp, S, nullptr, C.m, inm, ncols);
-    k_fdm_pass<T, true><<<grid, 256, smem, s>>>(tmp, z, S, nullptr, C.m, in1, ncols);
-  }
-  note_launches(2 * D - 1);  // the check below counts one
+  const int nl = fdm_passes<T, D>(f, z, (T*)C.tmp, coarse_S<T>(C), coarse_lam<T>(C), C.m, s);
+  note_launches(nl - 1);  // the check below counts one
   DCG_LAUNCH_CHECK();
   prof_end(p, prof, s, 2.0 * 2 * D * (double)nn * C.m,
            sizeof(T) * (2.0 * 2 * D * (double)nn + (double)C.m * C.m + nn), g_capturing);
@@ -1385,17 +1433,6 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
   }
   // RAS kernel shared memory opt-in: 227 KB per block minus the kernel's
   // static shared memory
-  {
-    const size_t need = (fp32 ? sizeof(float) : sizeof(double)) * 2 * 32 * (size_t)fdm_row(p->coarse.m);
-    if (need > 220 * 1024) {
-      set_error_msg("coarsest level too large for the fast-diagonalisation panels (use more levels)");
-      return DCG_ERR_UNSUPPORTED;
-    }
-    DCG_TRY(set_ras_smem(k_fdm_pass<float, true>));
-    DCG_TRY(set_ras_smem(k_fdm_pass<float, false>));
-    DCG_TRY(set_ras_smem(k_fdm_pass<double, true>));
-    DCG_TRY(set_ras_smem(k_fdm_pass<double, false>));
-  }
   DCG_TRY(set_ras_smem(k_ras_solve_tc<2>));
   DCG_TRY(set_ras_smem(k_ras_solve_tc<3>));
   DCG_TRY(set_ras_smem(k_ras_solve<float, 2, true>));
@@ -1595,11 +1632,6 @@ extern "C" int dcg_coarse_solve_static(dcg_problem* p, const double* f_dev, doub
     set_error_msg(buf);
     return DCG_ERR_INVALID_ARG;
   }
-  const size_t smem = sizeof(double) * 2 * 32 * (size_t)fdm_row(C.m);
-  if (smem > 220 * 1024) {
-    set_error_msg("dcg_coarse_solve_static: coarsest level too large for the pass panels");
-    return DCG_ERR_UNSUPPORTED;
-  }
   int dev = 0;
   DCG_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) {
@@ -1613,25 +1645,9 @@ extern "C" int dcg_coarse_solve_static(dcg_problem* p, const double* f_dev, doub
   }
   double* tmp = g_static_coarse_ptr[dev];
   cudaStream_t s = (cudaStream_t)stream;
-  const long long ncols = nn / C.m;
-  const dim3 grid((unsigned)((ncols + 31) / 32), (unsigned)((C.m + 31) / 32));
-  const long long in1 = 1, inm = C.m, inmm = (long long)C.m * C.m;
-  const double* S = C.S64;
-  const double* lam = C.lam64;
-  if (D == 2) {
-    k_fdm_pass<double, true><<<grid, 256, smem, s>>>(f_dev, tmp, S, nullptr, C.m, in1, ncols);
-    k_fdm_pass<double, false><<<grid, 256, smem, s>>>(tmp, z_dev, S, lam, C.m, inm, ncols);
-    k_fdm_pass<double, false><<<grid, 256, smem, s>>>(z_dev, tmp, S, nullptr, C.m, inm, ncols);
-    k_fdm_pass<double, true><<<grid, 256, smem, s>>>(tmp, z_dev, S, nullptr, C.m, in1, ncols);
-  } else {
-    k_fdm_pass<double, true><<<grid, 256, smem, s>>>(f_dev, tmp, S, nullptr, C.m, in1, ncols);
-    k_fdm_pass<double, false><<<grid, 256, smem, s>>>(tmp, z_dev, S, nullptr, C.m, inm, ncols);
-    k_fdm_pass<double, false><<<grid, 256, smem, s>>>(z_dev, tmp, S, lam, C.m, inmm, ncols);
-    k_fdm_pass<double, false><<<grid, 256, smem, s>>>(tmp, z_dev, S, nullptr, C.m, inmm, ncols);
-    k_fdm_pass<double, false><<<grid, 256, smem, s>>>(z_dev, tmp, S, nullptr, C.m, inm, ncols);
-    k_fdm_pass<double, true><<<grid, 256, smem, s>>>(tmp, z_dev, S, nullptr, C.m, in1, ncols);
-  }
-  note_launches(2 * D - 1);
+  const int nl = D == 2 ? fdm_passes<double, 2>(f_dev, z_dev, tmp, C.S64, C.lam64, C.m, s)
+                        : fdm_passes<double, 3>(f_dev, z_dev, tmp, C.S64, C.lam64, C.m, s);
+  note_launches(nl - 1);
   DCG_LAUNCH_CHECK();
   return DCG_OK;
 }
