@@ -684,8 +684,8 @@ __device__ __forceinline__ void lds4(const double* p, double (&v)[4]) {
 // Coarsest solve pass: S applied along one axis of the level grid, as the GEMM
 //   C[i][n] = sum_k S[k][i] B[k][n],  B[k][n] = in[(n / inner) m inner + k inner + n % inner]
 // (inner = m^axis; S is symmetric, so S[k][i] = S[i][k]), with optional
-// division by the eigenvalues in the epilogue. A CTA of 64 threads owns a
-// 32 x 32 tile of C, each thread a 4 x 4 register block; k runs through
+// division by the eigenvalues in the epilogue. A CTA of 128 threads owns a
+// 32 x 32 tile of C, each thread a 2 x 4 register block; k runs through
 // chunks of 32 staged in two shared-memory buffers, the next chunk held in
 // registers while the current one is multiplied. The k sum runs in order
 // 0..m-1 for every output. Rows of S and columns of B are read coalesced (for
@@ -694,13 +694,13 @@ __device__ __forceinline__ void lds4(const double* p, double (&v)[4]) {
 constexpr int kFdmTile = 32, kFdmLd = 36;
 
 template <typename T, bool AXIS0>
-__global__ void __launch_bounds__(64) k_fdm_pass(const T* __restrict__ in, T* __restrict__ out,
+__global__ void __launch_bounds__(128) k_fdm_pass(const T* __restrict__ in, T* __restrict__ out,
                                                   const T* __restrict__ S, const T* __restrict__ lam, int m,
                                                   long long inner, long long ncols) {
-  constexpr int KC = kFdmTile, LD = kFdmLd, R = KC * kFdmTile / 64;
+  constexpr int KC = kFdmTile, LD = kFdmLd, NT = 128, R = KC * kFdmTile / NT, KW = NT / 32;
   __shared__ __align__(16) T sA[2][KC][LD];
   __shared__ __align__(16) T sB[2][KC][LD];
-  const int tid = threadIdx.x, lane = tid & 31, half = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i0 = blockIdx.y * kFdmTile;
   const long long n0 = (long long)blockIdx.x * kFdmTile;
   const bool ia_ok = i0 + lane < m;
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(64) k_fdm_pass(const T* __restrict__ in, T* __
   auto load = [&](int k0) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int k = half + 2 * r;  // row of the chunk
+      const int k = warp + KW * r;  // row of the chunk
       const int kk = k0 + k;
       ra[r] = (kk < m && ia_ok) ? __ldg(S + (size_t)kk * m + i0 + lane) : (T)0;
       if (AXIS0) {
@@ -731,16 +731,16 @@ __global__ void __launch_bounds__(64) k_fdm_pass(const T* __restrict__ in, T* __
   auto store = [&](int buf) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int k = half + 2 * r;
+      const int k = warp + KW * r;
       sA[buf][k][lane] = ra[r];
       if (AXIS0) sB[buf][lane][k] = rb[r];
       else sB[buf][k][lane] = rb[r];
     }
   };
-  const int ti = (tid >> 3) * 4, tn = (tid & 7) * 4;
-  T acc[4][4];
+  const int ti = (tid >> 3) * 2, tn = (tid & 7) * 4;
+  T acc[2][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[a][q] = (T)0;
   const int nchunks = (m + KC - 1) / KC;
@@ -752,11 +752,11 @@ __global__ void __launch_bounds__(64) k_fdm_pass(const T* __restrict__ in, T* __
     if (c + 1 < nchunks) load((c + 1) * KC);
 #pragma unroll 8
     for (int k = 0; k < KC; ++k) {
-      T av[4], bv[4];
-      lds4(&sA[buf][k][ti], av);
+      T bv[4];
+      const T av[2] = {sA[buf][k][ti], sA[buf][k][ti + 1]};
       lds4(&sB[buf][k][tn], bv);
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[a][q] = fma(av[a], bv[q], acc[a][q]);
     }
@@ -764,7 +764,7 @@ __global__ void __launch_bounds__(64) k_fdm_pass(const T* __restrict__ in, T* __
     __syncthreads();
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
+  for (int a = 0; a < 2; ++a) {
     const int ii = i0 + ti + a;
     if (ii >= m) continue;
 #pragma unroll
@@ -789,17 +789,17 @@ int fdm_passes(const T* f, T* z, T* tmp, const T* S, const T* lam, int m, cudaSt
   const dim3 grid((unsigned)((ncols + kFdmTile - 1) / kFdmTile), (unsigned)((m + kFdmTile - 1) / kFdmTile));
   const long long in1 = 1, inm = m, inmm = (long long)m * m;
   if (D == 2) {
-    k_fdm_pass<T, true><<<grid, 64, 0, s>>>(f, tmp, S, nullptr, m, in1, ncols);
-    k_fdm_pass<T, false><<<grid, 64, 0, s>>>(tmp, z, S, lam, m, inm, ncols);
-    k_fdm_pass<T, false><<<grid, 64, 0, s>>>(z, tmp, S, nullptr, m, inm, ncols);
-    k_fdm_pass<T, true><<<grid, 64, 0, s>>>(tmp, z, S, nullptr, m, in1, ncols);
+    k_fdm_pass<T, true><<<grid, 128, 0, s>>>(f, tmp, S, nullptr, m, in1, ncols);
+    k_fdm_pass<T, false><<<grid, 128, 0, s>>>(tmp, z, S, lam, m, inm, ncols);
+    k_fdm_pass<T, false><<<grid, 128, 0, s>>>(z, tmp, S, nullptr, m, inm, ncols);
+    k_fdm_pass<T, true><<<grid, 128, 0, s>>>(tmp, z, S, nullptr, m, in1, ncols);
   } else {
-    k_fdm_pass<T, true><<<grid, 64, 0, s>>>(f, tmp, S, nullptr, m, in1, ncols);
-    k_fdm_pass<T, false><<<grid, 64, 0, s>>>(tmp, z, S, nullptr, m, inm, ncols);
-    k_fdm_pass<T, false><<<grid, 64, 0, s>>>(z, tmp, S, lam, m, inmm, ncols);
-    k_fdm_pass<T, false><<<grid, 64, 0, s>>>(tmp, z, S, nullptr, m, inmm, ncols);
-    k_fdm_pass<T, false><<<grid, 64, 0, s>>>(z, tmp, S, nullptr, m, inm, ncols);
-    k_fdm_pass<T, true><<<grid, 64, 0, s>>>(tmp, z, S, nullptr, m, in1, ncols);
+    k_fdm_pass<T, true><<<grid, 128, 0, s>>>(f, tmp, S, nullptr, m, in1, ncols);
+    k_fdm_pass<T, false><<<grid, 128, 0, s>>>(tmp, z, S, nullptr, m, inm, ncols);
+    k_fdm_pass<T, false><<<grid, 128, 0, s>>>(z, tmp, S, lam, m, inmm, ncols);
+    k_fdm_pass<T, false><<<grid, 128, 0, s>>>(tmp, z, S, nullptr, m, inmm, ncols);
+    k_fdm_pass<T, false><<<grid, 128, 0, s>>>(z, tmp, S, nullptr, m, inm, ncols);
+    k_fdm_pass<T, true><<<grid, 128, 0, s>>>(tmp, z, S, nullptr, m, in1, ncols);
   }
   return 2 * D;
 }
