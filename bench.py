@@ -342,8 +342,15 @@ def run_ours(args):
         extra["dcg_all_fp64_dt1e-6"] = {"s": time.perf_counter() - t0, "outer_its": st["outer_its"], "mg_levels": fp64_levels,
                                         "total_mg_cycles": st["total_mg_cycles"], "true_relres": st["true_relres"]}
         pf.close()
-    if not args.skip_batched:
-        extra["batched"] = batched_extra(args, opts, dcg, inputs, torch)
+    for key, skip, fn in [("batched", args.skip_batched, batched_extra), ("matrix_free_3d_256", args.skip_mf, mf_extra),
+                          ("bsr_3d_128", args.skip_3d, bsr3d_extra)]:
+        if skip:
+            continue
+        try:
+            extra[key] = fn(args, opts, dcg, inputs, torch)
+        except Exception as exc:  # an extra must not cost the headline line
+            extra[key] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+        torch.cuda.empty_cache()
     extra["spmv_fp64"] = {"GB_per_s": sp["bytes"] / (sp["ms"] / 1e3) / 1e9, "ms": sp["ms"] / max(1, sp["launches"])}
     extra["kernel_breakdown_warmup_ms"] = {c: round(v["ms"], 3) for c, v in breakdown.items()}
 
@@ -387,6 +394,81 @@ def run_ours(args):
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _timed(torch, fn, reps):
+    """Mean ms of fn() over reps calls, CUDA events on the current stream."""
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def mf_extra(args, opts, dcg, inputs, torch):
+    """Matrix-free 3D operator on 256^3 hexahedra (149,232,375 unknowns),
+    lognormal(0,1) element viscosity, dt = 1e-5: the product in FP32 and FP64
+    arithmetic, and one deflated-CG solve (FP32 products and W-cycle, FP64
+    outer recurrences and true residual)."""
+    n, dt = 256, 1e-5
+    nu = inputs.nu_elements(4, n ** 3)
+    prob = dcg.dcg_assemble(3, n, dt, nu_elem=nu, matrix_free=True)
+    N, nn = prob.N, prob.n_nodes
+    x = torch.from_numpy(inputs.rhs(0, N)).cuda()
+    y = torch.empty_like(x)
+    flops = 2.0 * (243 + 243 + 216) * nn
+    by = (72 + 72 + 8) * nn
+    out = {"n": n, "unknowns": N, "dt": dt, "nu": "lognormal(0,1) per element"}
+    for name, prec in [("fp32", dcg.DCG_MIXED), ("fp64", dcg.DCG_FP64)]:
+        ms = _timed(torch, lambda: dcg.dcg_spmv_prec(prob, x, y, prec), 10 if prec == dcg.DCG_MIXED else 3)
+        out["spmv_" + name] = {"ms": ms, "TFLOP_per_s": flops / (ms * 1e-3) / 1e12,
+                               "GB_per_s": by / (ms * 1e-3) / 1e9}
+    if not args.skip_mf_solve:
+        o = dcg.options(patch=4, overlap=1, m1=2, m2=2, max_levels=4, precision=dcg.DCG_MIXED,
+                        ras_inverse=dcg.DCG_INV_BF16)
+        t0 = time.perf_counter()
+        dcg.dcg_setup(prob, o)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        xs = torch.zeros_like(x)
+        t0 = time.perf_counter()
+        st = dcg.dcg_solve(prob, x, xs, tol=1e-8, max_it=args.max_it)
+        torch.cuda.synchronize()
+        out["dcg_mixed"] = {"s": time.perf_counter() - t0, "setup_s": setup_s, "levels": prob.levels,
+                            "outer_its": st["outer_its"], "total_mg_cycles": st["total_mg_cycles"],
+                            "restarts": st["restarts"], "true_relres": st["true_relres"], "status": st["status"]}
+    prob.close()
+    return out
+
+
+def bsr3d_extra(args, opts, dcg, inputs, torch):
+    """Assembled 3D operator on 128^3 hexahedra (18,458,712 unknowns, BSR
+    9x9), dt = 1e-4: deflated CG with the FP32 W-cycle and BF16 RAS inverses
+    on tensor cores against the all-FP64 solver."""
+    n, dt = 128, 1e-4
+    prob = dcg.dcg_assemble(3, n, dt)
+    f = torch.from_numpy(inputs.rhs(0, prob.N)).cuda()
+    out = {"n": n, "unknowns": prob.N, "dt": dt}
+    for name, prec, inv in [("mixed_bf16", dcg.DCG_MIXED, dcg.DCG_INV_BF16), ("fp64", dcg.DCG_FP64, dcg.DCG_INV_FP32)]:
+        dcg.dcg_setup(prob, dcg.options(patch=4, overlap=1, m1=2, m2=2, max_levels=4, precision=prec,
+                                        ras_inverse=inv))
+        x = torch.zeros_like(f)
+        t0 = time.perf_counter()
+        st = dcg.dcg_solve(prob, f, x, tol=1e-8, max_it=args.max_it)
+        torch.cuda.synchronize()
+        out[name] = {"s": time.perf_counter() - t0, "outer_its": st["outer_its"],
+                     "total_mg_cycles": st["total_mg_cycles"], "true_relres": st["true_relres"],
+                     "status": st["status"]}
+    y = torch.empty_like(f)
+    sp_ms = _timed(torch, lambda: dcg.dcg_spmv(prob, f, y), 10)
+    out["spmv_fp64_ms"] = sp_ms
+    out["spmv_fp64_GB_per_s"] = (prob.nnzb * 81 * 8 + prob.nnzb * 4 + 2 * prob.N * 8) / (sp_ms * 1e-3) / 1e9
+    prob.close()
+    return out
 
 
 def batched_extra(args, opts, dcg, inputs, torch):
@@ -516,6 +598,9 @@ def main():
     ap.add_argument("--skip-cg", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-mf", action="store_true")
+    ap.add_argument("--skip-mf-solve", action="store_true")
+    ap.add_argument("--skip-3d", action="store_true")
     ap.add_argument("--batched-problems", type=int, default=64)
     ap.add_argument("--batched-rhs", type=int, default=4)
     ap.add_argument("--levels", type=int, nargs="+", default=[2, 3, 4], help="hierarchy depths to autotune over")

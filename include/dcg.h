@@ -133,7 +133,9 @@ const char* dcg_last_error(void);
  * Section 3.2.1 on Q1). nu_elem: NULL for the uniform viscosity `nu`, else a
  * host array of n^dim per-element viscosities (elements lexicographic, x
  * fastest), copied during the call. matrix_free = 1 keeps only the element
- * data and applies A element by element (3D only); 0 stores BSR.
+ * data (1/nu per element) and applies A element by element, the element sum
+ * gathered per output node (3D meshes with n >= 4; DCG_ERR_UNSUPPORTED
+ * otherwise); 0 stores BSR.
  * On success *out owns the device data; free with dcg_destroy. */
 int dcg_assemble(const dcg_mesh* mesh, double dt, double nu, const double* nu_elem,
                  int matrix_free, dcg_problem** out, void* stream);
@@ -202,6 +204,15 @@ int dcg_export_values(const dcg_problem* p, double* values);
 
 /* y = A x (FP64, device arrays of N). */
 int dcg_spmv(const dcg_problem* p, const double* x_dev, double* y_dev, void* stream);
+
+/* y = A x with the arithmetic of `precision`: DCG_FP64, or DCG_MIXED for
+ * FP32 arithmetic on FP64 arrays, which only the matrix-free operator has
+ * (the sum over elements of Section 3.1's element blocks, regrouped per
+ * output node); DCG_ERR_UNSUPPORTED for DCG_MIXED on an assembled problem.
+ * Inside the deflated CG of a matrix-free problem set up with DCG_MIXED the
+ * products of the outer iterations run in FP32, the right-hand side
+ * projection, reconstruction and true residual in FP64. */
+int dcg_spmv_prec(const dcg_problem* p, const double* x_dev, double* y_dev, int precision, void* stream);
 
 /* q = V^T y (N -> n_nodes) and y = V q (n_nodes -> N), device arrays. */
 int dcg_extract(const dcg_problem* p, const double* y_dev, double* q_dev, void* stream);

@@ -192,8 +192,8 @@ int dcg_assemble(const dcg_mesh* mesh, double dt, double nu, const double* nu_el
     return DCG_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  if (matrix_free) {
-    set_error_msg("matrix-free assembly is not available in this build");
+  if (matrix_free && (mesh->dim != 3 || mesh->n < 4)) {
+    set_error_msg("dcg_assemble: the matrix-free operator is implemented for 3D meshes with n >= 4");
     return DCG_ERR_UNSUPPORTED;
   }
   if (nu_elem) {
@@ -217,7 +217,7 @@ int dcg_assemble(const dcg_mesh* mesh, double dt, double nu, const double* nu_el
   p->dt = dt;
   p->nu = nu;
   p->matrix_free = matrix_free;
-  if (p->nnzb >= (1LL << 31) || p->n_nodes >= (1LL << 31)) {
+  if ((!matrix_free && p->nnzb >= (1LL << 31)) || p->n_nodes >= (1LL << 31)) {
     delete p;
     set_error_msg("dcg_assemble: mesh too large for int32 BSR indices");
     return DCG_ERR_UNSUPPORTED;
@@ -532,6 +532,18 @@ int dcg_export_values(const dcg_problem* p, double* values) {
 int dcg_spmv(const dcg_problem* p, const double* x, double* y, void* stream) {
   if (!p || !x || !y) return DCG_ERR_INVALID_ARG;
   return spmv_plain(const_cast<dcg_problem*>(p), x, y, (cudaStream_t)stream);
+}
+
+int dcg_spmv_prec(const dcg_problem* p, const double* x, double* y, int precision, void* stream) {
+  if (!p || !x || !y || (precision != DCG_FP64 && precision != DCG_MIXED)) {
+    set_error_msg("dcg_spmv_prec: need problem, x, y and precision DCG_FP64 or DCG_MIXED");
+    return DCG_ERR_INVALID_ARG;
+  }
+  if (precision == DCG_MIXED && !p->matrix_free) {
+    set_error_msg("dcg_spmv_prec: FP32 arithmetic is implemented for the matrix-free operator only");
+    return DCG_ERR_UNSUPPORTED;
+  }
+  return spmv_plain(const_cast<dcg_problem*>(p), x, y, (cudaStream_t)stream, precision == DCG_MIXED);
 }
 
 int dcg_extract(const dcg_problem* p, const double* y, double* q, void* stream) {

@@ -294,17 +294,28 @@ void prof_clear_graph(dcg_problem* p);
 
 // launchers implemented in the .cu files
 int assemble_device(dcg_problem* p, const double* nu_elem_host, cudaStream_t s);
-int spmv_plain(dcg_problem* p, const double* x, double* y, cudaStream_t s);
+int spmv_plain(dcg_problem* p, const double* x, double* y, cudaStream_t s, bool lowp = false);
 // y = A x with dot(dv, y) into scal[slot] when dv != nullptr
 int spmv_dot(dcg_problem* p, const double* x, double* y, const double* dv, int slot, cudaStream_t s);
 // y = f - A x, ||y||^2 into scal[slot]
 int spmv_residual(dcg_problem* p, const double* f, const double* x, double* y, int slot, cudaStream_t s);
 // g = V^T A x, ||g||^2 into scal[slot]
-int spmv_vt(dcg_problem* p, const double* x, double* g, int slot, cudaStream_t s);
+int spmv_vt(dcg_problem* p, const double* x, double* g, int slot, cudaStream_t s, bool lowp = false);
 // q = A (x - V zh) (zh may be null => x), dot(x, q) into scal[slot]; if x null: q = A (V zh)
-int spmv_defl(dcg_problem* p, const double* x, const double* zh, double* q, int slot, cudaStream_t s);
+int spmv_defl(dcg_problem* p, const double* x, const double* zh, double* q, int slot, cudaStream_t s,
+              bool lowp = false);
 // y = f - A(V zh), ||y||^2 into scal[slot]
 int spmv_f_minus_avz(dcg_problem* p, const double* f, const double* zh, double* y, int slot, cudaStream_t s);
+// matrix-free 3D product (mf.cu): operand mode xm (0 x, 1 x - V zh, 2 V zh),
+// output mode om (0 y, 1 f - y, 2 V^T y), fused dot when `dot`, FP32
+// arithmetic when `lowp`
+int mf_product(dcg_problem* p, int xm, int om, bool dot, bool lowp, const double* x, const double* zh,
+               const double* f, double* y, const double* dvec, Reduce red, cudaStream_t s);
+// FP32 matrix-free products inside the outer iterations (mixed precision)
+// inner stencil of a matrix-free problem, and its check against the operator
+int mf_probe_stencil(dcg_problem* p, double* stencil, cudaStream_t s);
+int mf_check_stencil(dcg_problem* p, cudaStream_t s);
+inline bool mf_lowp(const dcg_problem* p) { return p->matrix_free && p->opts.precision == DCG_MIXED; }
 
 // vectors
 int vec_extract(dcg_problem* p, const double* y, double* q, int slot, cudaStream_t s);

@@ -1298,15 +1298,26 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
   const int D = p->dim;
   const dcg_options& o = p->opts;
   const bool fp32 = (o.precision == DCG_MIXED) && !exact_mode(p);
+  double* scal2 = nullptr;
+  DCG_CUDA(cudaMalloc(&scal2, sizeof(double) * 2 + sizeof(double) * 27 * 2));
+  Stencil<double> stJ{};
   if (p->matrix_free) {
-    set_error_msg("inner hierarchy for matrix-free problems is built by the matrix-free module");
-    return DCG_ERR_UNSUPPORTED;
-  }
+    // --- Z_J = V^T A V by probing the matrix-free operator (checked below,
+    // once the hierarchy exists, against the stencil on a full vector)
+    if (D != 3 || p->m < 3) {
+      cudaFree(scal2);
+      set_error_msg("matrix-free problems need a 3D mesh with n >= 4");
+      return DCG_ERR_UNSUPPORTED;
+    }
+    int st = mf_probe_stencil(p, stJ.c, s);
+    if (st != DCG_OK) {
+      cudaFree(scal2);
+      return st;
+    }
+  } else {
   // --- Z_J = V^T A V from the assembled matrix, checked to be one stencil
   double* rows = nullptr;
-  double* scal2 = nullptr;
   DCG_CUDA(cudaMalloc(&rows, sizeof(double) * 27 * p->n_nodes));
-  DCG_CUDA(cudaMalloc(&scal2, sizeof(double) * 2 + sizeof(double) * 27 * 2));
   DCG_CUDA(cudaMemsetAsync(scal2, 0, sizeof(double) * 2, s));
   const int g = grid_for(p->n_nodes, 256, 1 << 30);
   if (D == 2) k_zj_rows<2><<<g, 256, 0, s>>>(p->row_ptr, p->col_idx, p->vals, p->m, p->n_nodes, 1.0 / D, rows, scal2);
@@ -1335,7 +1346,6 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
   else k_zj_check<3><<<g, 256, 0, s>>>(rows, d_ref, p->m, p->n_nodes, scal2 + 1);
   DCG_LAUNCH_CHECK();
   double h_sc[2];
-  Stencil<double> stJ{};
   DCG_CUDA(cudaMemcpyAsync(h_sc, scal2, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
   DCG_CUDA(cudaMemcpyAsync(stJ.c, d_ref, sizeof(double) * 27, cudaMemcpyDeviceToHost, s));
   DCG_CUDA(cudaStreamSynchronize(s));
@@ -1350,6 +1360,7 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
     cudaFree(scal2);
     return DCG_ERR_UNSUPPORTED;
   }
+  }  // assembled
   // --- levels
   std::vector<int> sizes = exact_mode(p) ? std::vector<int>{p->n} : level_sizes(p->n, o.max_levels);
   const int J = (int)sizes.size();
@@ -1444,6 +1455,7 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
   DCG_TRY(set_ras_smem(k_ras_solve<double, 2, false>));
   DCG_TRY(set_ras_smem(k_ras_solve<double, 3, false>));
   DCG_CUDA(cudaStreamSynchronize(s));
+  if (p->matrix_free) DCG_TRY(mf_check_stencil(p, s));
   if (!exact_mode(p)) DCG_TRY(build_wcycle_graph(p));
   return DCG_OK;
 }

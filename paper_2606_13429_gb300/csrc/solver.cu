@@ -137,7 +137,7 @@ double inner_tol(const Ctx& c, double rnorm) {
 int pi_of_Ax(Ctx& c, const double* x, double* z, double tc, bool in_iter) {
   dcg_problem* p = c.p;
   SolverBuffers& b = p->sb;
-  DCG_TRY(spmv_vt(p, x, b.g, S_GG, c.s));
+  DCG_TRY(spmv_vt(p, x, b.g, S_GG, c.s, in_iter && mf_lowp(p)));
   DCG_TRY(vec_zero(z, p->n_nodes, c.s));
   int n = 0;
   DCG_TRY(mg_solve(p, b.g, z, tc, p->opts.inner_nmax, &n, c.s));
@@ -146,7 +146,6 @@ int pi_of_Ax(Ctx& c, const double* x, double* z, double tc, bool in_iter) {
   return DCG_OK;
 }
 
-// one FDCG pass: solve A x = f, x0 from x (if use_x0), result into x
 // One pass of Algorithm 2 from x0 (or zero). *stalled is set when the pass
 // ended because its recursive residual stopped falling (no value below 0.9 x
 // the best one for max(stall_window, its/4) iterations): the recursion of an
@@ -197,7 +196,7 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged, 
     const double tc = inner_tol(c, rnorm);
     // q = M_D d
     DCG_TRY(pi_of_Ax(c, b.d, b.zh, tc, true));
-    DCG_TRY(spmv_defl(p, b.d, b.zh, b.q, S_DQ, s));
+    DCG_TRY(spmv_defl(p, b.d, b.zh, b.q, S_DQ, s, mf_lowp(p)));
     if (fcginf) {
       // store d_k, q_k before the update (ring buffer of ndir_cap)
       const int slot = ndir % b.ndir_cap;
@@ -216,6 +215,14 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged, 
     const double dq = p->scal_host[S_DQ];
     const double rrn = p->scal_host[S_RRN];
     if (!(dq > 0.0) || !std::isfinite(dq) || !std::isfinite(rrn)) {
+      // FP32 matrix-free products: (d, M_D d) reaches the single-precision
+      // noise floor once the residual has fallen far enough; the update was
+      // skipped (alpha = 0) and the pass ends like a stall, restarting from
+      // the FP64 true residual
+      if (mf_lowp(p) && std::isfinite(dq) && std::isfinite(rrn)) {
+        *stalled = true;
+        break;
+      }
       c.st->status = DCG_ERR_BREAKDOWN;
       break;
     }

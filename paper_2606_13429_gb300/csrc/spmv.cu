@@ -184,11 +184,8 @@ __global__ void k_spmv(SpmvArgs A) {
 }
 
 template <int XM, int OM, bool DOT>
-int launch(dcg_problem* p, SpmvArgs a, cudaStream_t s) {
-  if (p->matrix_free) {
-    set_error_msg("BSR product requested on a matrix-free problem");
-    return DCG_ERR_UNSUPPORTED;
-  }
+int launch(dcg_problem* p, SpmvArgs a, cudaStream_t s, bool lowp = false) {
+  if (p->matrix_free) return mf_product(p, XM, OM, DOT, lowp, a.x, a.zh, a.f, a.y, a.dvec, a.red, s);
   a.row_ptr = p->row_ptr;
   a.col_idx = p->col_idx;
   a.vals = p->vals;
@@ -220,11 +217,11 @@ int launch(dcg_problem* p, SpmvArgs a, cudaStream_t s) {
 
 }  // namespace
 
-int spmv_plain(dcg_problem* p, const double* x, double* y, cudaStream_t s) {
+int spmv_plain(dcg_problem* p, const double* x, double* y, cudaStream_t s, bool lowp) {
   SpmvArgs a{};
   a.x = x;
   a.y = y;
-  return launch<XM_X, OM_Y, false>(p, a, s);
+  return launch<XM_X, OM_Y, false>(p, a, s, lowp);
 }
 
 int spmv_dot(dcg_problem* p, const double* x, double* y, const double* dv, int slot, cudaStream_t s) {
@@ -246,24 +243,24 @@ int spmv_residual(dcg_problem* p, const double* f, const double* x, double* y, i
   return launch<XM_X, OM_FMY, true>(p, a, s);
 }
 
-int spmv_vt(dcg_problem* p, const double* x, double* g, int slot, cudaStream_t s) {
+int spmv_vt(dcg_problem* p, const double* x, double* g, int slot, cudaStream_t s, bool lowp) {
   SpmvArgs a{};
   a.x = x;
   a.y = g;
   a.red = make_reduce(p, slot);
-  return launch<XM_X, OM_VT, true>(p, a, s);
+  return launch<XM_X, OM_VT, true>(p, a, s, lowp);
 }
 
-int spmv_defl(dcg_problem* p, const double* x, const double* zh, double* q, int slot, cudaStream_t s) {
+int spmv_defl(dcg_problem* p, const double* x, const double* zh, double* q, int slot, cudaStream_t s, bool lowp) {
   SpmvArgs a{};
   a.x = x;
   a.zh = zh;
   a.y = q;
   a.dvec = x;
   a.red = make_reduce(p, slot);
-  if (!x) return launch<XM_VZ, OM_Y, false>(p, a, s);
-  if (!zh) return launch<XM_X, OM_Y, true>(p, a, s);
-  return launch<XM_X_MINUS_VZ, OM_Y, true>(p, a, s);
+  if (!x) return launch<XM_VZ, OM_Y, false>(p, a, s, lowp);
+  if (!zh) return launch<XM_X, OM_Y, true>(p, a, s, lowp);
+  return launch<XM_X_MINUS_VZ, OM_Y, true>(p, a, s, lowp);
 }
 
 int spmv_f_minus_avz(dcg_problem* p, const double* f, const double* zh, double* y, int slot, cudaStream_t s) {

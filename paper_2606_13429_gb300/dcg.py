@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
         "dcg_export_pattern": (I, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "dcg_export_values": (I, [P, C.POINTER(C.c_double)]),
         "dcg_spmv": (I, [P, VP, VP, VP]),
+        "dcg_spmv_prec": (I, [P, VP, VP, I, VP]),
         "dcg_extract": (I, [P, VP, VP, VP]),
         "dcg_embed": (I, [P, VP, VP, VP]),
         "dcg_inner_apply": (I, [P, VP, VP, VP]),
@@ -286,6 +287,11 @@ def dcg_export_values(prob: Problem):
 
 def dcg_spmv(prob: Problem, x, y, stream=None):
     _check(load().dcg_spmv(prob.ptr, _dptr(x, prob.N, "x"), _dptr(y, prob.N, "y"), _stream(stream)), "dcg_spmv")
+
+
+def dcg_spmv_prec(prob: Problem, x, y, precision, stream=None):
+    _check(load().dcg_spmv_prec(prob.ptr, _dptr(x, prob.N, "x"), _dptr(y, prob.N, "y"), precision, _stream(stream)),
+           "dcg_spmv_prec")
 
 
 def dcg_extract(prob: Problem, y, q, stream=None):
