@@ -174,6 +174,9 @@ def compose_solve_time(t_spmv, t_wc, counts, n_unknowns):
 
 
 def run_ours(args):
+    global DTS
+    if args.dts:  # profiling runs: a subset of the step sizes
+        DTS = list(args.dts)
     import torch
     import torch.distributed as dist
     from paper_2606_13429_gb300 import build as B
@@ -378,7 +381,7 @@ def run_ours(args):
             "dtype": "f64 outer CG, f32 W-cycle" if prec == dcg.DCG_MIXED else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "mg_levels": best_levels,
+                       "mg_levels": best_levels, "dts": DTS,
                        "ras_products": "tcgen05 BF16 x BF16 -> FP32" if best_inv == dcg.DCG_INV_BF16 else "FP32 SIMT",
                        "autotune_inner_solve_s": {"levels=%d,%s" % (k[0], "bf16" if k[1] else "fp32"): v
                                                   for k, v in tune.items()},
@@ -601,6 +604,8 @@ def main():
     ap.add_argument("--skip-mf", action="store_true")
     ap.add_argument("--skip-mf-solve", action="store_true")
     ap.add_argument("--skip-3d", action="store_true")
+    ap.add_argument("--dts", type=float, nargs="+", default=None,
+                    help="step sizes of the timed solves (default 1e-6 1e-5 1e-4); for profiling runs")
     ap.add_argument("--batched-problems", type=int, default=64)
     ap.add_argument("--batched-rhs", type=int, default=4)
     ap.add_argument("--levels", type=int, nargs="+", default=[2, 3, 4], help="hierarchy depths to autotune over")

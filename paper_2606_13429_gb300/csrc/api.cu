@@ -55,7 +55,7 @@ int check_options(const dcg_options* o, int dim) {
 
 void free_solver_buffers(dcg_problem* p) {
   SolverBuffers& b = p->sb;
-  double* all[] = {b.xh, b.r, b.d, b.q, b.u, b.e, b.g, b.zh, b.zf, b.rin, b.dirs, b.qdirs, b.coef};
+  double* all[] = {b.xh, b.r, b.d, b.q, b.u, b.e, b.g, b.zh, b.zf, b.rin, b.dirs, b.qdirs, b.coef, b.w};
   for (double* v : all) cudaFree(v);
   b = SolverBuffers{};
 }
@@ -266,6 +266,7 @@ int dcg_setup(dcg_problem* p, const dcg_options* opts, void* stream) {
   DCG_TRY(alloc_vec(&b.u, N));
   DCG_TRY(alloc_vec(&b.e, N));
   if (opts->deflate) {
+    if (!p->matrix_free) DCG_TRY(alloc_vec(&b.w, N));
     DCG_TRY(alloc_vec(&b.g, nn));
     DCG_TRY(alloc_vec(&b.zh, nn));
     DCG_TRY(alloc_vec(&b.zf, nn));

@@ -190,11 +190,17 @@ struct Coarse {
   double* lam64 = nullptr; // eigenvalues of Z_1 (m^d)
   float* lam32 = nullptr;
   void* tmp = nullptr;     // work vector (m^d, precision of the cycle)
+  // FFT route when m + 1 is a power of two: log2(2(m+1)) (0: dense passes)
+  // and the twiddles e^{-2 pi i j / (2(m+1))}, j < m + 1
+  int log2n2 = 0;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
 };
 
 struct SolverBuffers {
   double *xh = nullptr, *r = nullptr, *d = nullptr, *q = nullptr, *u = nullptr, *e = nullptr;
   double *g = nullptr, *zh = nullptr, *zf = nullptr, *rin = nullptr;  // inner FP64 (n_nodes)
+  double* w = nullptr;     // operand d - V zh of the deflated product (assembled A)
   double* dirs = nullptr;  // FCG(inf): [ndir][N] directions
   double* qdirs = nullptr; // FCG(inf): [ndir][N] M_D directions
   double* coef = nullptr;  // FCG(inf): [ndir] coefficients
@@ -306,6 +312,13 @@ int spmv_defl(dcg_problem* p, const double* x, const double* zh, double* q, int 
               bool lowp = false);
 // y = f - A(V zh), ||y||^2 into scal[slot]
 int spmv_f_minus_avz(dcg_problem* p, const double* f, const double* zh, double* y, int slot, cudaStream_t s);
+// assembled operator: t = A x and g = V^T t in one pass (||g||^2 -> slot)
+int spmv_y_vt(dcg_problem* p, const double* x, double* t, double* g, int slot, cudaStream_t s);
+// q = t - A V zh through the divergence stencil (M_dev V = 0); (dv, q) -> slot
+int q_from_t(dcg_problem* p, const double* t, const double* zh, const double* dv, double* q, int slot,
+             cudaStream_t s);
+// divergence stencil G[p*3+q][offset] of the uniform Q1 mesh (d = 2, 3)
+void div_stencil(int d, int n, double (*gs)[27]);
 // matrix-free 3D product (mf.cu): operand mode xm (0 x, 1 x - V zh, 2 V zh),
 // output mode om (0 y, 1 f - y, 2 V^T y), fused dot when `dot`, FP32
 // arithmetic when `lowp`

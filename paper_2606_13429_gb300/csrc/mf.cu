@@ -215,47 +215,20 @@ __global__ void __launch_bounds__(kMX * mf_my<T>()) k_mf(MfArgs A) {
 // Host tables: divergence stencil and mass weights for mesh width h, step dt.
 void build_tables(MfArgs& a, int n, double dt) {
   const double h = 1.0 / n;
-  // 1D element integrals over [0, h]; local node 0 at the left end
-  auto M1 = [&](int i, int j) { return i == j ? h / 3.0 : h / 6.0; };
-  auto K1 = [&](int i, int j) { return i == j ? 1.0 / h : -1.0 / h; };
-  auto C1 = [&](int i, int /*j*/) { return i == 0 ? -0.5 : 0.5; };  // int psi_i' psi_j
   for (int o = 0; o < 27; ++o) {
     const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
     double mc = 1.0 / dt;
     for (int ax = 0; ax < 3; ++ax) mc *= off[ax] == 0 ? h / 3.0 : h / 6.0;
     a.mc64[o] = mc;
     a.mc32[o] = (float)mc;
-    for (int p = 0; p < 3; ++p)
-      for (int q = 0; q < 3; ++q) {
-        double sum = 0.0;
-        // elements holding the node and its neighbour: per axis s = 0 (node
-        // is the element's local node 1) and/or s = 1 (local node 0)
-        for (int s = 0; s < 8; ++s) {
-          const int sb[3] = {s & 1, (s >> 1) & 1, (s >> 2) & 1};
-          double v = 1.0;
-          bool ok = true;
-          for (int ax = 0; ax < 3 && ok; ++ax) {
-            const int la = sb[ax] == 0 ? 1 : 0, lb = la + off[ax];
-            if (lb < 0 || lb > 1) {
-              ok = false;
-              break;
-            }
-            double fct;
-            if (ax == p && ax == q) fct = K1(la, lb);
-            else if (ax == p) fct = C1(la, lb);
-            else if (ax == q) fct = C1(lb, la);
-            else fct = M1(la, lb);
-            v *= fct;
-          }
-          if (ok) sum += v;
-        }
-        a.gs64[p * 3 + q][o] = sum;
-        a.gs32[p * 3 + q][o] = (float)sum;
-      }
   }
+  div_stencil(3, n, a.gs64);
+  for (int pq = 0; pq < 9; ++pq)
+    for (int o = 0; o < 27; ++o) a.gs32[pq][o] = (float)a.gs64[pq][o];
 }
 
 __global__ void k_unit(double* v, long long i) { v[i] = 1.0; }
+
 
 // deterministic test pattern in [-1, 1)
 __global__ void k_pattern_vec(double* v, long long n) {

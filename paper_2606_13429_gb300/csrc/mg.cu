@@ -778,28 +778,168 @@ __global__ void __launch_bounds__(128) k_fdm_pass(const T* __restrict__ in, T* _
   }
 }
 
+// ---------------------------------------------------------------------------
+// FFT route for the same passes when N = m + 1 is a power of two: applying S
+// along an axis is a type-I discrete sine transform of each grid line,
+//   (S x)_k = sqrt(2/N) sum_j x_j sin(pi j k / N),  j, k = 1..N-1,
+// which is -Im(V_k) / 2 (times sqrt(2/N)) for V the length-2N discrete
+// Fourier transform of the odd extension (0, x_1..x_{N-1}, 0, -x_{N-1}..-x_1).
+// Two real lines share one complex transform (line a in the real part, b in
+// the imaginary part: a's sums are -Im(V)/2, b's are Re(V)/2). A CTA takes
+// COLS consecutive lines, builds their extensions in shared memory in
+// bit-reversed order and runs the log2(2N) radix-2 butterfly stages there,
+// twiddles staged from a table made on the host in FP64.
+// O(m^d log m) work instead of the dense passes' O(m^(d+1)).
+
+template <typename T>
+struct cplx;
+template <>
+struct cplx<float> {
+  using type = float2;
+};
+template <>
+struct cplx<double> {
+  using type = double2;
+};
+
+template <typename T, bool AXIS0, int COLS>
+__global__ void __launch_bounds__(256) k_dst_pass(const T* __restrict__ in, T* __restrict__ out,
+                                                  const typename cplx<T>::type* __restrict__ tw,
+                                                  const T* __restrict__ lam, int m, int log2n2, long long inner,
+                                                  long long ncols, T scale) {
+  using C2 = typename cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char dst_smem[];
+  const int N2 = 1 << log2n2, N = N2 >> 1;
+  C2* buf = reinterpret_cast<C2*>(dst_smem);  // [COLS / 2][N2]
+  C2* stw = buf + (COLS / 2) * N2;             // [N]
+  T* bufr = reinterpret_cast<T*>(buf);
+  const long long n0 = (long long)blockIdx.x * COLS;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) stw[j] = tw[j];
+  // the two zeros of every extension (positions 0 and N; bit reversal keeps
+  // 0 at 0 and sends N to 1)
+  for (int t = threadIdx.x; t < COLS / 2; t += blockDim.x) {
+    buf[t * N2] = C2{(T)0, (T)0};
+    buf[t * N2 + 1] = C2{(T)0, (T)0};
+  }
+  // line c, entry k (j = k + 1) -> positions j and 2N - j (negated)
+  const int total = COLS * m;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int c, k;
+    if (AXIS0) {  // lines are contiguous: k fastest
+      c = t / m;
+      k = t - c * m;
+    } else {      // lines are strided: consecutive threads take consecutive lines
+      k = t / COLS;
+      c = t - k * COLS;
+    }
+    const long long nb = n0 + c;
+    T v = (T)0;
+    if (nb < ncols) {
+      const long long hi = nb / inner;
+      v = __ldg(in + hi * m * inner + (long long)k * inner + (nb - hi * inner));
+    }
+    const int j = k + 1;
+    const int p = c >> 1, part = c & 1;
+    const unsigned r1 = __brev((unsigned)j) >> (32 - log2n2);
+    const unsigned r2 = __brev((unsigned)(N2 - j)) >> (32 - log2n2);
+    bufr[2 * ((size_t)p * N2 + r1) + part] = v;
+    bufr[2 * ((size_t)p * N2 + r2) + part] = -v;
+  }
+  __syncthreads();
+  for (int s = 0; s < log2n2; ++s) {
+    const int h = 1 << s;
+    for (int b = threadIdx.x; b < (COLS / 2) * N; b += blockDim.x) {
+      const int p = b / N, q = b - p * N;
+      const int pos = q & (h - 1);
+      const int i0 = ((q >> s) << (s + 1)) + pos, i1 = i0 + h;
+      const C2 w = stw[pos << (log2n2 - 1 - s)];
+      const C2 a = buf[p * N2 + i0], x = buf[p * N2 + i1];
+      const T tr = w.x * x.x - w.y * x.y, ti = w.x * x.y + w.y * x.x;
+      buf[p * N2 + i0] = C2{a.x + tr, a.y + ti};
+      buf[p * N2 + i1] = C2{a.x - tr, a.y - ti};
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int c, k;
+    if (AXIS0) {
+      c = t / m;
+      k = t - c * m;
+    } else {
+      k = t / COLS;
+      c = t - k * COLS;
+    }
+    const long long nb = n0 + c;
+    if (nb >= ncols) continue;
+    const C2 V = buf[(c >> 1) * N2 + k + 1];
+    T v = (c & 1) ? V.x : -V.y;
+    v *= scale;  // sqrt(2/N) / 2
+    const long long hi = nb / inner;
+    const long long o = hi * m * inner + (long long)k * inner + (nb - hi * inner);
+    out[o] = lam ? v / lam[o] : v;
+  }
+}
+
+template <typename T, int COLS>
+size_t dst_smem_bytes(int log2n2) {
+  const size_t N2 = (size_t)1 << log2n2;
+  return sizeof(typename cplx<T>::type) * ((COLS / 2) * N2 + N2 / 2);
+}
+
+// one DST pass: 2 lines per CTA for long transforms (enough CTAs to fill the
+// GPU), 8 for short ones (enough work per CTA)
+template <typename T>
+void dst_pass(const T* in, T* out, const typename cplx<T>::type* tw, const T* lam, int m, int log2n2,
+              long long inner, long long ncols, T scale, cudaStream_t s) {
+  if (log2n2 >= 9) {
+    const unsigned grid = (unsigned)((ncols + 1) / 2);
+    const size_t smem = dst_smem_bytes<T, 2>(log2n2);
+    if (inner == 1) k_dst_pass<T, true, 2><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, 1, ncols, scale);
+    else k_dst_pass<T, false, 2><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, inner, ncols, scale);
+  } else {
+    const unsigned grid = (unsigned)((ncols + 7) / 8);
+    const size_t smem = dst_smem_bytes<T, 8>(log2n2);
+    if (inner == 1) k_dst_pass<T, true, 8><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, 1, ncols, scale);
+    else k_dst_pass<T, false, 8><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, inner, ncols, scale);
+  }
+}
+
 // z = S^(x)D Lambda^-1 S^(x)D f on the coarsest grid: 2D passes along
 // axes 0, 1 (with Lambda^-1), 1, 0; 3D along 0, 1, 2 (Lambda^-1), 2, 1, 0.
-// tmp: scratch of m^D values. Returns the number of kernels launched.
+// tmp: scratch of m^D values. With log2n2 > 0 (m + 1 a power of two) the
+// passes are sine transforms by FFT, else dense GEMM passes with S.
+// Returns the number of kernels launched.
 template <typename T, int D>
-int fdm_passes(const T* f, T* z, T* tmp, const T* S, const T* lam, int m, cudaStream_t s) {
+int fdm_passes(const T* f, T* z, T* tmp, const T* S, const T* lam, const typename cplx<T>::type* tw, int log2n2,
+               int m, cudaStream_t s) {
   long long nn = 1;
   for (int k = 0; k < D; ++k) nn *= m;
   const long long ncols = nn / m;
-  const dim3 grid((unsigned)((ncols + kFdmTile - 1) / kFdmTile), (unsigned)((m + kFdmTile - 1) / kFdmTile));
   const long long in1 = 1, inm = m, inmm = (long long)m * m;
+  const T* src[6];
+  T* dst[6];
+  long long inner[6];
+  const T* lm[6];
   if (D == 2) {
-    k_fdm_pass<T, true><<<grid, 128, 0, s>>>(f, tmp, S, nullptr, m, in1, ncols);
-    k_fdm_pass<T, false><<<grid, 128, 0, s>>>(tmp, z, S, lam, m, inm, ncols);
-    k_fdm_pass<T, false><<<grid, 128, 0, s>>>(z, tmp, S, nullptr, m, inm, ncols);
-    k_fdm_pass<T, true><<<grid, 128, 0, s>>>(tmp, z, S, nullptr, m, in1, ncols);
+    const T* s2[4] = {f, tmp, z, tmp};
+    T* d2[4] = {tmp, z, tmp, z};
+    const long long i2[4] = {in1, inm, inm, in1};
+    for (int k = 0; k < 4; ++k) { src[k] = s2[k]; dst[k] = d2[k]; inner[k] = i2[k]; lm[k] = k == 1 ? lam : nullptr; }
   } else {
-    k_fdm_pass<T, true><<<grid, 128, 0, s>>>(f, tmp, S, nullptr, m, in1, ncols);
-    k_fdm_pass<T, false><<<grid, 128, 0, s>>>(tmp, z, S, nullptr, m, inm, ncols);
-    k_fdm_pass<T, false><<<grid, 128, 0, s>>>(z, tmp, S, lam, m, inmm, ncols);
-    k_fdm_pass<T, false><<<grid, 128, 0, s>>>(tmp, z, S, nullptr, m, inmm, ncols);
-    k_fdm_pass<T, false><<<grid, 128, 0, s>>>(z, tmp, S, nullptr, m, inm, ncols);
-    k_fdm_pass<T, true><<<grid, 128, 0, s>>>(tmp, z, S, nullptr, m, in1, ncols);
+    const T* s3[6] = {f, tmp, z, tmp, z, tmp};
+    T* d3[6] = {tmp, z, tmp, z, tmp, z};
+    const long long i3[6] = {in1, inm, inmm, inmm, inm, in1};
+    for (int k = 0; k < 6; ++k) { src[k] = s3[k]; dst[k] = d3[k]; inner[k] = i3[k]; lm[k] = k == 2 ? lam : nullptr; }
+  }
+  if (log2n2 > 0) {
+    const T scale = (T)(0.5 * std::sqrt(2.0 / (m + 1)));
+    for (int k = 0; k < 2 * D; ++k) dst_pass<T>(src[k], dst[k], tw, lm[k], m, log2n2, inner[k], ncols, scale, s);
+  } else {
+    const dim3 grid((unsigned)((ncols + kFdmTile - 1) / kFdmTile), (unsigned)((m + kFdmTile - 1) / kFdmTile));
+    for (int k = 0; k < 2 * D; ++k) {
+      if (inner[k] == 1) k_fdm_pass<T, true><<<grid, 128, 0, s>>>(src[k], dst[k], S, lm[k], m, 1, ncols);
+      else k_fdm_pass<T, false><<<grid, 128, 0, s>>>(src[k], dst[k], S, lm[k], m, inner[k], ncols);
+    }
   }
   return 2 * D;
 }
@@ -1131,17 +1271,29 @@ template <>
 const float* coarse_lam<float>(const Coarse& c) { return c.lam32; }
 template <>
 const double* coarse_lam<double>(const Coarse& c) { return c.lam64; }
+template <typename T>
+const typename cplx<T>::type* coarse_tw(const Coarse& c);
+template <>
+const float2* coarse_tw<float>(const Coarse& c) { return c.tw32; }
+template <>
+const double2* coarse_tw<double>(const Coarse& c) { return c.tw64; }
 
 template <typename T, int D>
 int coarse_solve_t(dcg_problem* p, const T* f, T* z, cudaStream_t s) {
   const Coarse& C = p->coarse;
   const long long nn = ipow(C.m, D);
   const int prof = prof_begin(p, PC_COARSE, s, g_capturing);
-  const int nl = fdm_passes<T, D>(f, z, (T*)C.tmp, coarse_S<T>(C), coarse_lam<T>(C), C.m, s);
+  const int nl = fdm_passes<T, D>(f, z, (T*)C.tmp, coarse_S<T>(C), coarse_lam<T>(C), coarse_tw<T>(C), C.log2n2, C.m, s);
   note_launches(nl - 1);  // the check below counts one
   DCG_LAUNCH_CHECK();
-  prof_end(p, prof, s, 2.0 * 2 * D * (double)nn * C.m,
-           sizeof(T) * (2.0 * 2 * D * (double)nn + (double)C.m * C.m + nn), g_capturing);
+  // algorithmic work: dense passes 2 m flops per value and pass; FFT passes
+  // 5 N2 log2(N2) flops per complex transform of length N2 (two lines each)
+  const double flops = C.log2n2 > 0
+                           ? 2.0 * D * ((double)nn / C.m / 2.0) * 5.0 * (double)(1 << C.log2n2) * C.log2n2
+                           : 2.0 * 2 * D * (double)nn * C.m;
+  const double bytes = sizeof(T) * (2.0 * 2 * D * (double)nn + nn) +
+                       (C.log2n2 > 0 ? 0.0 : sizeof(T) * (double)C.m * C.m);
+  prof_end(p, prof, s, flops, bytes, g_capturing);
   return DCG_OK;
 }
 
@@ -1287,6 +1439,7 @@ void mg_free(dcg_problem* p) {
   p->levels.clear();
   cudaFree(p->coarse.S64); cudaFree(p->coarse.S32); cudaFree(p->coarse.lam64); cudaFree(p->coarse.lam32);
   cudaFree(p->coarse.tmp);
+  cudaFree(p->coarse.tw64); cudaFree(p->coarse.tw32);
   p->coarse = Coarse{};
   if (p->mg.wexec) cudaGraphExecDestroy(p->mg.wexec);
   if (p->mg.cap) cudaStreamDestroy(p->mg.cap);
@@ -1434,6 +1587,42 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
     if (D == 2) k_fdm_setup<2><<<gg, 256, 0, s>>>(C.m, C.S64, C.lam64);
     else k_fdm_setup<3><<<gg, 256, 0, s>>>(C.m, C.S64, C.lam64);
     DCG_LAUNCH_CHECK();
+    // FFT route: m + 1 a power of two, transforms of length 2(m+1) <= 2048
+    C.log2n2 = 0;
+    if (((C.m + 1) & C.m) == 0 && C.m + 1 <= 1024) {
+      int l = 1;
+      while ((1 << l) < 2 * (C.m + 1)) ++l;
+      C.log2n2 = l;
+      const int N = C.m + 1;
+      std::vector<double2> tw(N);
+      std::vector<float2> tw32(N);
+      for (int j = 0; j < N; ++j) {
+        const double a = M_PI * (double)j / (double)N;  // 2 pi j / (2N)
+        tw[j] = make_double2(std::cos(a), -std::sin(a));
+        tw32[j] = make_float2((float)tw[j].x, (float)tw[j].y);
+      }
+      DCG_CUDA(cudaMalloc(&C.tw64, sizeof(double2) * N));
+      DCG_CUDA(cudaMalloc(&C.tw32, sizeof(float2) * N));
+      DCG_CUDA(cudaMemcpyAsync(C.tw64, tw.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, s));
+      DCG_CUDA(cudaMemcpyAsync(C.tw32, tw32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice, s));
+      DCG_CUDA(cudaStreamSynchronize(s));  // the host tables go out of scope
+      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<float, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)dst_smem_bytes<float, 2>(11)));
+      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<float, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)dst_smem_bytes<float, 2>(11)));
+      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<double, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)dst_smem_bytes<double, 2>(11)));
+      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<double, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)dst_smem_bytes<double, 2>(11)));
+      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<float, true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)dst_smem_bytes<float, 8>(8)));
+      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<float, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)dst_smem_bytes<float, 8>(8)));
+      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<double, true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)dst_smem_bytes<double, 8>(8)));
+      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<double, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)dst_smem_bytes<double, 8>(8)));
+    }
     if (fp32) {
       DCG_CUDA(cudaMalloc(&C.S32, sizeof(float) * C.m * C.m));
       DCG_CUDA(cudaMalloc(&C.lam32, sizeof(float) * nn));
@@ -1657,8 +1846,8 @@ extern "C" int dcg_coarse_solve_static(dcg_problem* p, const double* f_dev, doub
   }
   double* tmp = g_static_coarse_ptr[dev];
   cudaStream_t s = (cudaStream_t)stream;
-  const int nl = D == 2 ? fdm_passes<double, 2>(f_dev, z_dev, tmp, C.S64, C.lam64, C.m, s)
-                        : fdm_passes<double, 3>(f_dev, z_dev, tmp, C.S64, C.lam64, C.m, s);
+  const int nl = D == 2 ? fdm_passes<double, 2>(f_dev, z_dev, tmp, C.S64, C.lam64, C.tw64, C.log2n2, C.m, s)
+                        : fdm_passes<double, 3>(f_dev, z_dev, tmp, C.S64, C.lam64, C.tw64, C.log2n2, C.m, s);
   note_launches(nl - 1);
   DCG_LAUNCH_CHECK();
   return DCG_OK;

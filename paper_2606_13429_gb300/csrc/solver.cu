@@ -134,6 +134,18 @@ double inner_tol(const Ctx& c, double rnorm) {
 }
 
 // zh = MG(V^T A x) into `z` (zeroed first), counting cycles
+// z = MG(g) from zero (Algorithm 3 on the inner system), counting cycles
+int inner_solve(Ctx& c, double* z, double tc, bool in_iter) {
+  dcg_problem* p = c.p;
+  SolverBuffers& b = p->sb;
+  DCG_TRY(vec_zero(z, p->n_nodes, c.s));
+  int n = 0;
+  DCG_TRY(mg_solve(p, b.g, z, tc, p->opts.inner_nmax, &n, c.s));
+  c.st->total_mg_cycles += n;
+  if (in_iter) c.st->iter_mg_cycles += n;
+  return DCG_OK;
+}
+
 int pi_of_Ax(Ctx& c, const double* x, double* z, double tc, bool in_iter) {
   dcg_problem* p = c.p;
   SolverBuffers& b = p->sb;
@@ -194,9 +206,18 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged, 
   while (!*converged && c.st->outer_its < c.max_it) {
     const double rnorm = std::sqrt(rr);
     const double tc = inner_tol(c, rnorm);
-    // q = M_D d
-    DCG_TRY(pi_of_Ax(c, b.d, b.zh, tc, true));
-    DCG_TRY(spmv_defl(p, b.d, b.zh, b.q, S_DQ, s, mf_lowp(p)));
+    // q = M_D d = A (d - V MG(V^T A d))
+    if (b.w) {
+      // assembled A: one pass over the matrix gives t = A d (kept in w) and
+      // g = V^T t; then q = t - A V zh = t - K_div V zh by stencil, since the
+      // mass part of A annihilates V (saves the second product)
+      DCG_TRY(spmv_y_vt(p, b.d, b.w, b.g, S_GG, s));
+      DCG_TRY(inner_solve(c, b.zh, tc, true));
+      DCG_TRY(q_from_t(p, b.w, b.zh, b.d, b.q, S_DQ, s));
+    } else {
+      DCG_TRY(pi_of_Ax(c, b.d, b.zh, tc, true));
+      DCG_TRY(spmv_defl(p, b.d, b.zh, b.q, S_DQ, s, mf_lowp(p)));
+    }
     if (fcginf) {
       // store d_k, q_k before the update (ring buffer of ndir_cap)
       const int slot = ndir % b.ndir_cap;

@@ -21,7 +21,7 @@ namespace dcg {
 namespace {
 
 enum XMode { XM_X = 0, XM_X_MINUS_VZ = 1, XM_VZ = 2 };
-enum OMode { OM_Y = 0, OM_FMY = 1, OM_VT = 2 };
+enum OMode { OM_Y = 0, OM_FMY = 1, OM_VT = 2, OM_YVT = 3 };
 
 struct SpmvArgs {
   const int* row_ptr;
@@ -32,6 +32,7 @@ struct SpmvArgs {
   const double* zh;
   const double* f;
   double* y;
+  double* g;           // V^T y for OM_YVT
   const double* dvec;  // dot(dvec, y) for OM_Y
   double isd;          // 1/sqrt(d)
   Reduce red;
@@ -146,6 +147,7 @@ __global__ void k_spmv(SpmvArgs A) {
   constexpr int B = D * D;
   constexpr int NW = (OM == OM_VT) ? D : B;
   __shared__ double s_rows[NW][32];
+  static_assert(OM != OM_YVT || NW == B, "all rows");
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const int R = (OM == OM_VT) ? w * D + w : w;
@@ -169,6 +171,20 @@ __global__ void k_spmv(SpmvArgs A) {
         if (DOT) part[0] = fma(g, g, part[0]);
       }
       __syncthreads();
+    } else if (OM == OM_YVT) {
+      // all rows of t = A x, and g = V^T t from the diagonal-component rows
+      if (a < A.n_nodes) A.y[a * B + R] = acc;
+      s_rows[w][lane] = acc;
+      __syncthreads();
+      if (w == 0 && a < A.n_nodes) {
+        double s = s_rows[0][lane];
+#pragma unroll
+        for (int l = 1; l < D; ++l) s += s_rows[l * D + l][lane];
+        const double g = s * A.isd;
+        A.g[a] = g;
+        if (DOT) part[0] = fma(g, g, part[0]);
+      }
+      __syncthreads();
     } else if (a < A.n_nodes) {
       const long long row = a * B + R;
       double out = acc;
@@ -183,6 +199,22 @@ __global__ void k_spmv(SpmvArgs A) {
   if (DOT) grid_reduce<1>(part, A.red);
 }
 
+// w = x - V zh (node-major, the d diagonal components of each node shifted):
+// formed once per node instead of once per stored block that reads it, which
+// keeps the FP64 arithmetic of the deflated product at that of A x
+template <int D>
+__global__ void k_x_minus_vz(const double* __restrict__ x, const double* __restrict__ zh, double* __restrict__ w,
+                             long long nn, double isd) {
+  constexpr int B = D * D;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn * B;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long a = t / B;
+    const int c = (int)(t - a * B);
+    const double v = x[t];
+    w[t] = (c % (D + 1) == 0) ? __dsub_rn(v, __dmul_rn(isd, __ldg(zh + a))) : v;
+  }
+}
+
 template <int XM, int OM, bool DOT>
 int launch(dcg_problem* p, SpmvArgs a, cudaStream_t s, bool lowp = false) {
   if (p->matrix_free) return mf_product(p, XM, OM, DOT, lowp, a.x, a.zh, a.f, a.y, a.dvec, a.red, s);
@@ -195,12 +227,13 @@ int launch(dcg_problem* p, SpmvArgs a, cudaStream_t s, bool lowp = false) {
   // algorithmic work: structural FMAs and the bytes the product must move
   const int D = p->dim, B = D * D;
   const double nnzb = (double)p->nnzb, nn = (double)p->n_nodes, N = (double)p->N;
-  const int rows_read = (OM == OM_VT) ? D : B;
+  const int rows_read = (OM == OM_VT) ? D : B;  // OM_YVT reads all rows
   const double fma_blk = (OM == OM_VT) ? D * (2 * D - 1) : (D == 2 ? 10 : 33);
   double bytes = nnzb * (rows_read * B * 8.0 + 4.0) + (nn + 1) * 4.0;
   bytes += (XM == XM_VZ) ? nn * 8.0 : N * 8.0;          // operand
   if (XM == XM_X_MINUS_VZ) bytes += nn * 8.0;           // zh
   bytes += (OM == OM_VT) ? nn * 8.0 : N * 8.0;          // output
+  if (OM == OM_YVT) bytes += nn * 8.0;                  // g
   if (OM == OM_FMY) bytes += N * 8.0;                   // f
   const int prof = prof_begin(p, PC_SPMV, s);
   if (p->dim == 2) {
@@ -260,7 +293,130 @@ int spmv_defl(dcg_problem* p, const double* x, const double* zh, double* q, int 
   a.red = make_reduce(p, slot);
   if (!x) return launch<XM_VZ, OM_Y, false>(p, a, s, lowp);
   if (!zh) return launch<XM_X, OM_Y, true>(p, a, s, lowp);
+  if (!p->matrix_free && p->sb.w) {
+    const double isd = 1.0 / std::sqrt((double)p->dim);
+    const int g = grid_for(p->N, 256, 8192);
+    const int prof = prof_begin(p, PC_VEC, s);
+    if (p->dim == 2) k_x_minus_vz<2><<<g, 256, 0, s>>>(x, zh, p->sb.w, p->n_nodes, isd);
+    else k_x_minus_vz<3><<<g, 256, 0, s>>>(x, zh, p->sb.w, p->n_nodes, isd);
+    DCG_LAUNCH_CHECK();
+    prof_end(p, prof, s, 2.0 * p->n_nodes * p->dim, 8.0 * (2.0 * p->N + p->n_nodes));
+    a.x = p->sb.w;  // dvec stays x: the fused dot is (x, A w)
+    return launch<XM_X, OM_Y, true>(p, a, s, lowp);
+  }
   return launch<XM_X_MINUS_VZ, OM_Y, true>(p, a, s, lowp);
+}
+
+int spmv_y_vt(dcg_problem* p, const double* x, double* t, double* g, int slot, cudaStream_t s) {
+  SpmvArgs a{};
+  a.x = x;
+  a.y = t;
+  a.g = g;
+  a.red = make_reduce(p, slot);
+  return launch<XM_X, OM_YVT, true>(p, a, s);
+}
+
+// Divergence part of the element blocks summed over elements: for the uniform
+// Q1 mesh a constant 3^d-point stencil per component pair (p, q),
+//   G[p][q][o] = sum over the elements holding a and a+o of int d_p phi_a d_q phi_{a+o},
+// each element integral a product of 1D factors (mass h/3 | h/6, stiffness
+// +-1/h, mixed +-1/2). Offsets o = ox + 3 oy (+ 9 oz in 3D), each shifted by
+// +1; entries for p, q >= d or o >= 3^d are zero.
+void div_stencil(int d, int n, double (*gs)[27]) {
+  const double h = 1.0 / n;
+  for (int o = 0; o < 27; ++o) {
+    const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, d == 3 ? o / 9 - 1 : 0};
+    for (int p = 0; p < 3; ++p)
+      for (int q = 0; q < 3; ++q) {
+        double sum = 0.0;
+        const bool used = p < d && q < d && (d == 3 || o < 9);
+        for (int sb = 0; used && sb < (1 << d); ++sb) {
+          double v = 1.0;
+          bool ok = true;
+          for (int ax = 0; ax < d && ok; ++ax) {
+            const int la = ((sb >> ax) & 1) == 0 ? 1 : 0, lb = la + off[ax];
+            if (lb < 0 || lb > 1) {
+              ok = false;
+              break;
+            }
+            double f;
+            if (ax == p && ax == q) f = la == lb ? 1.0 / h : -1.0 / h;
+            else if (ax == p) f = la == 0 ? -0.5 : 0.5;
+            else if (ax == q) f = lb == 0 ? -0.5 : 0.5;
+            else f = la == lb ? h / 3.0 : h / 6.0;
+            v *= f;
+          }
+          if (ok) sum += v;
+        }
+        gs[p * 3 + q][o] = sum;
+      }
+  }
+}
+
+namespace {
+
+struct DivStencil {
+  double c[9][27];
+};
+
+// q = t - A V zh for the assembled operator, with A V zh = K_div V zh (the
+// mass part annihilates V exactly): component (k, p) of node a is
+//   t - (1/sqrt d) sum_o G[p][k][o] zh[a+o].
+// Also reduces (dv, q).
+template <int D>
+__global__ void k_q_from_t(const double* __restrict__ t, const double* __restrict__ zh, const double* __restrict__ dv,
+                           double* __restrict__ q, DivStencil G, int m, long long nn, double isd, Reduce red) {
+  constexpr int B = D * D, NO = D == 2 ? 9 : 27;
+  double part[1] = {0.0};
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nn; a += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    long long r = a;
+    c[0] = (int)(r % m);
+    r /= m;
+    c[1] = (int)(r % m);
+    c[2] = D > 2 ? (int)(r / m) : 0;
+    double zn[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+      const int x = c[0] + ox, y = c[1] + oy, z = c[2] + oz;
+      const bool in = x >= 0 && x < m && y >= 0 && y < m && (D == 2 || (z >= 0 && z < m));
+      zn[o] = in ? __ldg(zh + x + (long long)m * (y + (long long)m * (D > 2 ? z : 0))) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+      for (int p = 0; p < D; ++p) {
+        double acc = 0.0;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+          const int off[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+          if (p != k && (off[p] == 0 || off[k] == 0)) continue;  // cross stencil vanishes there
+          acc = fma(G.c[p * 3 + k][o], zn[o], acc);
+        }
+        const long long row = a * B + k * D + p;
+        const double v = t[row] - isd * acc;
+        q[row] = v;
+        part[0] = fma(dv[row], v, part[0]);
+      }
+  }
+  grid_reduce<1>(part, red);
+}
+
+}  // namespace
+
+int q_from_t(dcg_problem* p, const double* t, const double* zh, const double* dv, double* q, int slot,
+             cudaStream_t s) {
+  DivStencil G;
+  div_stencil(p->dim, p->n, G.c);
+  const double isd = 1.0 / std::sqrt((double)p->dim);
+  const int g = grid_for(p->n_nodes, 256, 4096);
+  const int prof = prof_begin(p, PC_VEC, s);
+  if (p->dim == 2) k_q_from_t<2><<<g, 256, 0, s>>>(t, zh, dv, q, G, p->m, p->n_nodes, isd, make_reduce(p, slot));
+  else k_q_from_t<3><<<g, 256, 0, s>>>(t, zh, dv, q, G, p->m, p->n_nodes, isd, make_reduce(p, slot));
+  DCG_LAUNCH_CHECK();
+  prof_end(p, prof, s, 2.0 * p->N * (p->dim == 2 ? 6.5 : 15.0), 8.0 * (3.0 * p->N + p->n_nodes));
+  return DCG_OK;
 }
 
 int spmv_f_minus_avz(dcg_problem* p, const double* f, const double* zh, double* y, int slot, cudaStream_t s) {

@@ -86,3 +86,12 @@ def test_batched_and_autotune_reject_bad_arguments_without_gpu(lib):
     assert lib.dcg_autotune(None, C.byref(base), None, 1e-6, 3, C.byref(best), C.byref(ms), None) == \
         dcg.DCG_ERR_INVALID_ARG
     assert "dcg_autotune" in dcg.last_error()
+
+
+def test_matrix_free_limits_rejected_without_gpu(lib):
+    out = C.c_void_p()
+    for dim, n in [(2, 16), (3, 3)]:
+        mesh = dcg.dcg_mesh(dim, n)
+        assert lib.dcg_assemble(C.byref(mesh), 1e-3, 1.0, None, 1, C.byref(out), None) == dcg.DCG_ERR_UNSUPPORTED
+        assert "matrix-free" in dcg.last_error()
+    assert lib.dcg_spmv_prec(None, None, None, dcg.DCG_MIXED, None) == dcg.DCG_ERR_INVALID_ARG
