@@ -802,29 +802,66 @@ struct cplx<double> {
   using type = double2;
 };
 
-template <typename T, bool AXIS0, int COLS>
+// position of transform entry e in shared memory: one pad slot every 32
+// entries, so the bit-reversed scatter of consecutive entries (which would
+// land 32 entries apart) spreads over the banks
+__device__ __forceinline__ int dst_pad(int e) { return e + (e >> 5); }
+
+// the odd extension of the COLS lines' values v (entry k of line c, k < m)
+// into bit-reversed, padded positions
+template <typename T>
+__device__ __forceinline__ void dst_scatter(T* bufr, int NP, int N2, int log2n2, int c, int k, T v) {
+  const int j = k + 1, p = c >> 1, part = c & 1;
+  const int r1 = (int)(__brev((unsigned)j) >> (32 - log2n2));
+  const int r2 = (int)(__brev((unsigned)(N2 - j)) >> (32 - log2n2));
+  bufr[2 * (p * NP + dst_pad(r1)) + part] = v;
+  bufr[2 * (p * NP + dst_pad(r2)) + part] = -v;
+}
+
+template <typename C2>
+__device__ __forceinline__ void dst_stages(C2* buf, const C2* stw, int NP, int N, int log2n2, int pairs) {
+  for (int s = 0; s < log2n2; ++s) {
+    const int h = 1 << s;
+    for (int b = threadIdx.x; b < pairs * N; b += blockDim.x) {
+      const int p = b / N, q = b - p * N;
+      const int pos = q & (h - 1);
+      const int i0 = ((q >> s) << (s + 1)) + pos, i1 = i0 + h;
+      const C2 w = stw[pos << (log2n2 - 1 - s)];
+      C2* e0 = buf + p * NP + dst_pad(i0);
+      C2* e1 = buf + p * NP + dst_pad(i1);
+      const C2 a = *e0, x = *e1;
+      const auto tr = w.x * x.x - w.y * x.y, ti = w.x * x.y + w.y * x.x;
+      *e0 = C2{a.x + tr, a.y + ti};
+      *e1 = C2{a.x - tr, a.y - ti};
+    }
+    __syncthreads();
+  }
+}
+
+// One pass (or, with FUSED, the two passes along the same axis around the
+// eigenvalue division: out = S (Lambda^-1 o (S in)) line by line).
+template <typename T, bool AXIS0, int COLS, bool FUSED>
 __global__ void __launch_bounds__(256) k_dst_pass(const T* __restrict__ in, T* __restrict__ out,
                                                   const typename cplx<T>::type* __restrict__ tw,
                                                   const T* __restrict__ lam, int m, int log2n2, long long inner,
                                                   long long ncols, T scale) {
   using C2 = typename cplx<T>::type;
+  constexpr int kMaxPer = 8;  // entries per thread kept in registers between the fused transforms
   extern __shared__ __align__(16) unsigned char dst_smem[];
-  const int N2 = 1 << log2n2, N = N2 >> 1;
-  C2* buf = reinterpret_cast<C2*>(dst_smem);  // [COLS / 2][N2]
-  C2* stw = buf + (COLS / 2) * N2;             // [N]
+  const int N2 = 1 << log2n2, N = N2 >> 1, NP = N2 + (N2 >> 5);
+  C2* buf = reinterpret_cast<C2*>(dst_smem);  // [COLS / 2][NP]
+  C2* stw = buf + (COLS / 2) * NP;             // [N]
   T* bufr = reinterpret_cast<T*>(buf);
   const long long n0 = (long long)blockIdx.x * COLS;
   for (int j = threadIdx.x; j < N; j += blockDim.x) stw[j] = tw[j];
   // the two zeros of every extension (positions 0 and N; bit reversal keeps
   // 0 at 0 and sends N to 1)
   for (int t = threadIdx.x; t < COLS / 2; t += blockDim.x) {
-    buf[t * N2] = C2{(T)0, (T)0};
-    buf[t * N2 + 1] = C2{(T)0, (T)0};
+    buf[t * NP] = C2{(T)0, (T)0};
+    buf[t * NP + 1] = C2{(T)0, (T)0};
   }
-  // line c, entry k (j = k + 1) -> positions j and 2N - j (negated)
   const int total = COLS * m;
-  for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    int c, k;
+  auto entry = [&](int t, int& c, int& k) {
     if (AXIS0) {  // lines are contiguous: k fastest
       c = t / m;
       k = t - c * m;
@@ -832,76 +869,107 @@ __global__ void __launch_bounds__(256) k_dst_pass(const T* __restrict__ in, T* _
       k = t / COLS;
       c = t - k * COLS;
     }
+  };
+  auto gidx = [&](long long nb, int k) {
+    const long long hi = nb / inner;
+    return hi * m * inner + (long long)k * inner + (nb - hi * inner);
+  };
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    int c, k;
+    entry(t, c, k);
     const long long nb = n0 + c;
-    T v = (T)0;
-    if (nb < ncols) {
-      const long long hi = nb / inner;
-      v = __ldg(in + hi * m * inner + (long long)k * inner + (nb - hi * inner));
-    }
-    const int j = k + 1;
-    const int p = c >> 1, part = c & 1;
-    const unsigned r1 = __brev((unsigned)j) >> (32 - log2n2);
-    const unsigned r2 = __brev((unsigned)(N2 - j)) >> (32 - log2n2);
-    bufr[2 * ((size_t)p * N2 + r1) + part] = v;
-    bufr[2 * ((size_t)p * N2 + r2) + part] = -v;
+    const T v = nb < ncols ? __ldg(in + gidx(nb, k)) : (T)0;
+    dst_scatter(bufr, NP, N2, log2n2, c, k, v);
   }
   __syncthreads();
-  for (int s = 0; s < log2n2; ++s) {
-    const int h = 1 << s;
-    for (int b = threadIdx.x; b < (COLS / 2) * N; b += blockDim.x) {
-      const int p = b / N, q = b - p * N;
-      const int pos = q & (h - 1);
-      const int i0 = ((q >> s) << (s + 1)) + pos, i1 = i0 + h;
-      const C2 w = stw[pos << (log2n2 - 1 - s)];
-      const C2 a = buf[p * N2 + i0], x = buf[p * N2 + i1];
-      const T tr = w.x * x.x - w.y * x.y, ti = w.x * x.y + w.y * x.x;
-      buf[p * N2 + i0] = C2{a.x + tr, a.y + ti};
-      buf[p * N2 + i1] = C2{a.x - tr, a.y - ti};
+  dst_stages(buf, stw, NP, N, log2n2, COLS / 2);
+  if (FUSED) {
+    // sine sums of the first transform, divided by the eigenvalues, become
+    // the input of the second (entries held in registers across the rebuild)
+    T keep[kMaxPer];
+    int i = 0;
+    for (int t = threadIdx.x; t < total; t += blockDim.x, ++i) {
+      int c, k;
+      entry(t, c, k);
+      const long long nb = n0 + c;
+      const C2 V = buf[(c >> 1) * NP + dst_pad(k + 1)];
+      T v = ((c & 1) ? V.x : -V.y) * scale;
+      if (nb < ncols) v = v / lam[gidx(nb, k)];
+      else v = (T)0;
+      keep[i] = v;
     }
     __syncthreads();
+    for (int t = threadIdx.x; t < COLS / 2; t += blockDim.x) {
+      buf[t * NP] = C2{(T)0, (T)0};
+      buf[t * NP + 1] = C2{(T)0, (T)0};
+    }
+    i = 0;
+    for (int t = threadIdx.x; t < total; t += blockDim.x, ++i) {
+      int c, k;
+      entry(t, c, k);
+      dst_scatter(bufr, NP, N2, log2n2, c, k, keep[i]);
+    }
+    __syncthreads();
+    dst_stages(buf, stw, NP, N, log2n2, COLS / 2);
   }
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     int c, k;
-    if (AXIS0) {
-      c = t / m;
-      k = t - c * m;
-    } else {
-      k = t / COLS;
-      c = t - k * COLS;
-    }
+    entry(t, c, k);
     const long long nb = n0 + c;
     if (nb >= ncols) continue;
-    const C2 V = buf[(c >> 1) * N2 + k + 1];
+    const C2 V = buf[(c >> 1) * NP + dst_pad(k + 1)];
     T v = (c & 1) ? V.x : -V.y;
     v *= scale;  // sqrt(2/N) / 2
-    const long long hi = nb / inner;
-    const long long o = hi * m * inner + (long long)k * inner + (nb - hi * inner);
-    out[o] = lam ? v / lam[o] : v;
+    const long long o = gidx(nb, k);
+    out[o] = (!FUSED && lam) ? v / lam[o] : v;
   }
 }
 
 template <typename T, int COLS>
 size_t dst_smem_bytes(int log2n2) {
   const size_t N2 = (size_t)1 << log2n2;
-  return sizeof(typename cplx<T>::type) * ((COLS / 2) * N2 + N2 / 2);
+  return sizeof(typename cplx<T>::type) * ((COLS / 2) * (N2 + (N2 >> 5)) + N2 / 2);
 }
 
-// one DST pass: 2 lines per CTA for long transforms (enough CTAs to fill the
-// GPU), 8 for short ones (enough work per CTA)
-template <typename T>
+// one DST pass (FUSED: two passes around Lambda^-1): 2 lines per CTA for long
+// transforms (enough CTAs to fill the GPU), 8 for short ones. The route takes
+// 2(m+1) <= 2048, so a CTA holds at most 2 x 1023 (or 8 x 127) entries: at
+// most 8 per thread, as the fused kernel's register copy needs.
+template <typename T, bool FUSED>
 void dst_pass(const T* in, T* out, const typename cplx<T>::type* tw, const T* lam, int m, int log2n2,
               long long inner, long long ncols, T scale, cudaStream_t s) {
   if (log2n2 >= 9) {
     const unsigned grid = (unsigned)((ncols + 1) / 2);
     const size_t smem = dst_smem_bytes<T, 2>(log2n2);
-    if (inner == 1) k_dst_pass<T, true, 2><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, 1, ncols, scale);
-    else k_dst_pass<T, false, 2><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, inner, ncols, scale);
+    if (inner == 1)
+      k_dst_pass<T, true, 2, FUSED><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, 1, ncols, scale);
+    else
+      k_dst_pass<T, false, 2, FUSED><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, inner, ncols, scale);
   } else {
     const unsigned grid = (unsigned)((ncols + 7) / 8);
     const size_t smem = dst_smem_bytes<T, 8>(log2n2);
-    if (inner == 1) k_dst_pass<T, true, 8><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, 1, ncols, scale);
-    else k_dst_pass<T, false, 8><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, inner, ncols, scale);
+    if (inner == 1)
+      k_dst_pass<T, true, 8, FUSED><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, 1, ncols, scale);
+    else
+      k_dst_pass<T, false, 8, FUSED><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, inner, ncols, scale);
   }
+}
+
+// shared-memory opt-in of the sine-transform kernels for the largest
+// transform the route takes (2(m+1) = 2048)
+template <typename T>
+int set_dst_smem() {
+  const int big = (int)dst_smem_bytes<T, 2>(11), small = (int)dst_smem_bytes<T, 8>(8);
+  const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, true, 2, false>, attr, big));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, false, 2, false>, attr, big));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, true, 2, true>, attr, big));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, false, 2, true>, attr, big));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, true, 8, false>, attr, small));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, false, 8, false>, attr, small));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, true, 8, true>, attr, small));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, false, 8, true>, attr, small));
+  return DCG_OK;
 }
 
 // z = S^(x)D Lambda^-1 S^(x)D f on the coarsest grid: 2D passes along
@@ -932,8 +1000,21 @@ int fdm_passes(const T* f, T* z, T* tmp, const T* S, const T* lam, const typenam
     for (int k = 0; k < 6; ++k) { src[k] = s3[k]; dst[k] = d3[k]; inner[k] = i3[k]; lm[k] = k == 2 ? lam : nullptr; }
   }
   if (log2n2 > 0) {
+    // the two passes along the last axis, around Lambda^-1, run as one
+    // kernel: 2D axes 0, 1+1, 0 and 3D 0, 1, 2+2, 1, 0 (2D - 1 launches)
     const T scale = (T)(0.5 * std::sqrt(2.0 / (m + 1)));
-    for (int k = 0; k < 2 * D; ++k) dst_pass<T>(src[k], dst[k], tw, lm[k], m, log2n2, inner[k], ncols, scale, s);
+    if (D == 2) {
+      dst_pass<T, false>(f, z, tw, nullptr, m, log2n2, in1, ncols, scale, s);
+      dst_pass<T, true>(z, tmp, tw, lam, m, log2n2, inm, ncols, scale, s);
+      dst_pass<T, false>(tmp, z, tw, nullptr, m, log2n2, in1, ncols, scale, s);
+    } else {
+      dst_pass<T, false>(f, z, tw, nullptr, m, log2n2, in1, ncols, scale, s);
+      dst_pass<T, false>(z, tmp, tw, nullptr, m, log2n2, inm, ncols, scale, s);
+      dst_pass<T, true>(tmp, z, tw, lam, m, log2n2, inmm, ncols, scale, s);
+      dst_pass<T, false>(z, tmp, tw, nullptr, m, log2n2, inm, ncols, scale, s);
+      dst_pass<T, false>(tmp, z, tw, nullptr, m, log2n2, in1, ncols, scale, s);
+    }
+    return 2 * D - 1;
   } else {
     const dim3 grid((unsigned)((ncols + kFdmTile - 1) / kFdmTile), (unsigned)((m + kFdmTile - 1) / kFdmTile));
     for (int k = 0; k < 2 * D; ++k) {
@@ -1606,22 +1687,8 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
       DCG_CUDA(cudaMemcpyAsync(C.tw64, tw.data(), sizeof(double2) * N, cudaMemcpyHostToDevice, s));
       DCG_CUDA(cudaMemcpyAsync(C.tw32, tw32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice, s));
       DCG_CUDA(cudaStreamSynchronize(s));  // the host tables go out of scope
-      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<float, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)dst_smem_bytes<float, 2>(11)));
-      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<float, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)dst_smem_bytes<float, 2>(11)));
-      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<double, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)dst_smem_bytes<double, 2>(11)));
-      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<double, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)dst_smem_bytes<double, 2>(11)));
-      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<float, true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)dst_smem_bytes<float, 8>(8)));
-      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<float, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)dst_smem_bytes<float, 8>(8)));
-      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<double, true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)dst_smem_bytes<double, 8>(8)));
-      DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<double, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)dst_smem_bytes<double, 8>(8)));
+      DCG_TRY(set_dst_smem<float>());
+      DCG_TRY(set_dst_smem<double>());
     }
     if (fp32) {
       DCG_CUDA(cudaMalloc(&C.S32, sizeof(float) * C.m * C.m));
