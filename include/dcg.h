@@ -74,7 +74,8 @@ extern "C" {
 #define DCG_MIXED  1  /* W-cycle (stencils, transfers, RAS) in FP32; outer CG FP64 */
 
 #define DCG_INV_FP32  0  /* RAS patch inverses stored FP32 (mixed mode) */
-#define DCG_INV_BF16  1  /* RAS patch inverses BF16 x FP32 residuals on tensor cores */
+#define DCG_INV_BF16  1  /* RAS patch inverses and box residuals in BF16, products on tcgen05
+                             tensor cores with FP32 accumulation (mixed mode) */
 
 #define DCG_RAS_MULTIPLICITY  0  /* D_i = 1/multiplicity (Section 4.2) */
 #define DCG_RAS_RESTRICTED    1  /* D_i = 1 on the core tile, 0 on the overlap */

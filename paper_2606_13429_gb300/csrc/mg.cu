@@ -1026,23 +1026,29 @@ int fdm_passes(const T* f, T* z, T* tmp, const T* S, const T* lam, const typenam
 }
 
 // FP64 fine residual r = g - Z_J z, stored into the cycle's level-J RHS (in
-// the cycle precision); zeroes the level-J iterate; reduces ||r||^2, ||g||^2.
+// the cycle precision); zeroes the level-J iterate; reduces ||r||^2 and, when
+// with_g, ||g||^2 (g does not change within an inner solve). FP64 arithmetic
+// is scarce on this GPU: with an FP32 cycle the squares of r are summed from
+// its FP32 copy (the norm only feeds the stopping test).
 template <typename T, int D>
 __global__ void k_inner_residual(Stencil<double> st, const double* __restrict__ g, const double* __restrict__ z,
                                  T* __restrict__ fJ, T* __restrict__ zJ, double* __restrict__ r64, int m, long long nn,
-                                 Reduce red) {
+                                 Reduce red, bool with_g) {
   double part[2] = {0.0, 0.0};
+  T rr = (T)0;
   for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nn; a += (long long)gridDim.x * blockDim.x) {
     int c[3];
     coords_of<D>(a, m, c);
     const double ga = g[a];
     const double r = ga - stencil_apply<double, D>(st, z, m, c);
-    if (fJ) fJ[a] = (T)r;
+    const T rt = (T)r;
+    if (fJ) fJ[a] = rt;
     if (zJ) zJ[a] = (T)0;
     if (r64) r64[a] = r;
-    part[0] = fma(r, r, part[0]);
-    part[1] = fma(ga, ga, part[1]);
+    rr = fma(rt, rt, rr);
+    if (with_g) part[1] = fma(ga, ga, part[1]);
   }
+  part[0] = (double)rr;
   grid_reduce<2>(part, red);
 }
 
@@ -1734,15 +1740,15 @@ int mg_inner_apply(dcg_problem* p, const double* z, double* y, cudaStream_t s) {
 namespace {
 
 template <typename T>
-int inner_residual(dcg_problem* p, const double* g, const double* z, cudaStream_t s) {
+int inner_residual(dcg_problem* p, const double* g, const double* z, cudaStream_t s, bool with_g = true) {
   Level& L = p->levels.back();
   const int grid = grid_for(L.nn, 256, 4096);
   Reduce red = make_reduce(p, S_TMP0);  // S_TMP0 <- ||r||^2, S_TMP1 <- ||g||^2
   const int prof = prof_begin(p, PC_INNER_RES, s);
   if (p->dim == 2)
-    k_inner_residual<T, 2><<<grid, 256, 0, s>>>(L.st64, g, z, (T*)L.f, (T*)L.z, nullptr, L.m, L.nn, red);
+    k_inner_residual<T, 2><<<grid, 256, 0, s>>>(L.st64, g, z, (T*)L.f, (T*)L.z, nullptr, L.m, L.nn, red, with_g);
   else
-    k_inner_residual<T, 3><<<grid, 256, 0, s>>>(L.st64, g, z, (T*)L.f, (T*)L.z, nullptr, L.m, L.nn, red);
+    k_inner_residual<T, 3><<<grid, 256, 0, s>>>(L.st64, g, z, (T*)L.f, (T*)L.z, nullptr, L.m, L.nn, red, with_g);
   DCG_LAUNCH_CHECK();
   prof_end(p, prof, s, 2.0 * ipow(3, p->dim) * (double)L.nn, (16.0 + 2.0 * sizeof(T)) * L.nn);
   return DCG_OK;
@@ -1792,12 +1798,13 @@ int mg_solve(dcg_problem* p, const double* g, double* z, double tol, int nmax, i
   if (exact_mode(p)) return exact_solve(p, g, z, s);
   const bool fp32 = p->mg.fp32;
   int n = 0;
+  double gn = 0.0;
   for (;;) {
-    DCG_TRY(fp32 ? inner_residual<float>(p, g, z, s) : inner_residual<double>(p, g, z, s));
+    DCG_TRY(fp32 ? inner_residual<float>(p, g, z, s, n == 0) : inner_residual<double>(p, g, z, s, n == 0));
     DCG_TRY(read_scalars(p, s));
     if (n > 0 && p->prof.mask) prof_flush_graph(p);  // the replay before this read
     const double rn = std::sqrt(p->scal_host[S_TMP0]);
-    const double gn = std::sqrt(p->scal_host[S_TMP1]);
+    if (n == 0) gn = std::sqrt(p->scal_host[S_TMP1]);
     if (!(gn > 0.0)) break;
     if (!(rn / gn > tol) || n >= nmax) break;
     DCG_TRY(run_wcycle(p, s));
