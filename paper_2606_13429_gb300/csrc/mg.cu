@@ -1471,7 +1471,10 @@ int wcycle_t(dcg_problem* p, int k, cudaStream_t s, bool z_zero) {
            sizeof(T) * (4.0 * L.nn + Lc.nn), g_capturing);
   DCG_CUDA(cudaMemsetAsync(Lc.z, 0, sizeof(T) * Lc.nn, s));
   DCG_TRY((wcycle_t<T, D>(p, k - 1, s, true)));
-  DCG_TRY((wcycle_t<T, D>(p, k - 1, s, false)));
+  // Algorithm 4's second recursive call W_{k-1}(r_c, e1): on the coarsest
+  // level W is the exact solve, which ignores the initial guess, so the second
+  // call would repeat the first bit for bit and is skipped there
+  if (k - 1 > 1) DCG_TRY((wcycle_t<T, D>(p, k - 1, s, false)));
   prof = prof_begin(p, PC_TRANSFER, s, g_capturing);
   k_prolong_add<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>((const T*)Lc.z, (T*)L.z, L.m, Lc.m, L.nn);
   DCG_LAUNCH_CHECK();
