@@ -548,6 +548,16 @@ def roofline(dominant, dom, peaks, peak_src, tensor=False):
             traffic = ent["dram_bytes_per_launch"]
     except Exception:
         pass
+    if dominant == "inner_res" and secs > 0:
+        # FP64 stencil residual: bound by FP64 issue (ncu: FP64 pipe ~83% busy),
+        # against the nominal GB300 FP64 rate (2 FMA / clock / SM)
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = NUM_SMS * 4 * mhz * 1e6 / 1e12
+        achieved = dom["flops"] / secs / 1e12
+        return {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": "FP64 FMA: 152 SMs x 2 FMA x 2 flops x %.0f MHz (nominal 1.26 TFLOP/s)" % mhz,
+                "launches": dom["launches"], "algorithmic_flops_per_launch": dom["flops"] / max(1, dom["launches"])}
     if dominant in ("spmv", "vec", "ras_update", "transfer", "inner_res") or secs <= 0:
         achieved = dom["bytes"] / secs / 1e9 if secs > 0 else 0.0
         peak = peaks["hbm_gbs"]

@@ -59,6 +59,11 @@ struct Reduce {
 };
 constexpr int kMaxVals = 4;
 constexpr int kMaxRedCtas = 65536;
+// grid of the kernels that end in grid_reduce: a few CTAs per SM, each
+// thread looping over several items, so that the per-thread share of the
+// block reduction (FP64 shuffles and adds, which this GPU issues slowly)
+// is amortised
+constexpr int kRedGrid = 8 * 152;
 
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /*[32*NV]*/) {

@@ -1745,7 +1745,7 @@ namespace {
 template <typename T>
 int inner_residual(dcg_problem* p, const double* g, const double* z, cudaStream_t s, bool with_g = true) {
   Level& L = p->levels.back();
-  const int grid = grid_for(L.nn, 256, 4096);
+  const int grid = grid_for(L.nn, 256, kRedGrid);
   Reduce red = make_reduce(p, S_TMP0);  // S_TMP0 <- ||r||^2, S_TMP1 <- ||g||^2
   const int prof = prof_begin(p, PC_INNER_RES, s);
   if (p->dim == 2)

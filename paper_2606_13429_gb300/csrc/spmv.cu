@@ -223,7 +223,7 @@ int launch(dcg_problem* p, SpmvArgs a, cudaStream_t s, bool lowp = false) {
   a.vals = p->vals;
   a.n_nodes = p->n_nodes;
   a.isd = 1.0 / sqrt((double)p->dim);
-  const int grid = grid_for(p->n_nodes, 32);
+  const int grid = grid_for(p->n_nodes, 32, DOT ? 2 * kRedGrid : kMaxRedCtas);
   // algorithmic work: structural FMAs and the bytes the product must move
   const int D = p->dim, B = D * D;
   const double nnzb = (double)p->nnzb, nn = (double)p->n_nodes, N = (double)p->N;
@@ -410,7 +410,7 @@ int q_from_t(dcg_problem* p, const double* t, const double* zh, const double* dv
   DivStencil G;
   div_stencil(p->dim, p->n, G.c);
   const double isd = 1.0 / std::sqrt((double)p->dim);
-  const int g = grid_for(p->n_nodes, 256, 4096);
+  const int g = grid_for(p->n_nodes, 256, kRedGrid);
   const int prof = prof_begin(p, PC_VEC, s);
   if (p->dim == 2) k_q_from_t<2><<<g, 256, 0, s>>>(t, zh, dv, q, G, p->m, p->n_nodes, isd, make_reduce(p, slot));
   else k_q_from_t<3><<<g, 256, 0, s>>>(t, zh, dv, q, G, p->m, p->n_nodes, isd, make_reduce(p, slot));

@@ -45,7 +45,7 @@ __global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b
 }  // namespace
 
 int vec_extract(dcg_problem* p, const double* y, double* q, int slot, cudaStream_t s) {
-  const int g = grid_for(p->n_nodes, kRedThreads, 4096);
+  const int g = grid_for(p->n_nodes, kRedThreads, kRedGrid);
   const double isd = 1.0 / sqrt((double)p->dim);
   Reduce red = make_reduce(p, slot < 0 ? S_TMP0 : slot);
   if (p->dim == 2) k_extract<2><<<g, kRedThreads, 0, s>>>(y, q, p->n_nodes, isd, red, slot >= 0);
@@ -64,7 +64,7 @@ int vec_embed(dcg_problem* p, const double* q, double* y, cudaStream_t s) {
 }
 
 int vec_dot(dcg_problem* p, const double* a, const double* b, long long n, int slot, cudaStream_t s) {
-  const int g = grid_for(n, kRedThreads, 4096);
+  const int g = grid_for(n, kRedThreads, kRedGrid);
   k_dot<<<g, kRedThreads, 0, s>>>(a, b, n, make_reduce(p, slot));
   DCG_LAUNCH_CHECK();
   return DCG_OK;
