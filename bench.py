@@ -197,6 +197,9 @@ def run_ours(args):
     ws, rank, local = dist_init()
     if ws > 1:
         dist.init_process_group("nccl")
+        # replicas: the headline solve only; the single-GPU characterisations
+        # (plain CG sweep, FP64 solver, batched, matrix-free, 3D) stay at N = 1
+        args.skip_cg = args.skip_fp64 = args.skip_batched = args.skip_mf = args.skip_3d = True
     torch.cuda.set_device(local)
     B.build()
     dcg.load()
@@ -492,12 +495,32 @@ def batched_extra(args, opts, dcg, inputs, torch):
     nrhs = args.batched_rhs
     plist = inputs.batched_problems(11, args.batched_problems)
     probs, fs = [], []
+    tuned, choices = {}, {}
+    t_tune = time.perf_counter()
     for p, (nb, dtb) in enumerate(plist):
         pr = dcg.dcg_assemble(2, nb, dtb)
-        dcg.dcg_setup(pr, opts)
+        f0 = torch.from_numpy(inputs.rhs(5, pr.N, p=p, r=0)).cuda()
+        if args.batched_no_tune:
+            dcg.dcg_setup(pr, opts)
+        elif nb not in tuned:
+            # the library's autotuner (hierarchy depth, RAS tile and overlap,
+            # inverse precision) once per mesh size: the inner system does not
+            # depend on dt, so one problem of each size stands for the others
+            best, _ = dcg.dcg_autotune(pr, f0, opts, inner_tol=1e-10, reps=2)
+            tuned[nb] = best
+        else:
+            dcg.dcg_setup(pr, tuned[nb])
+        if nb in tuned:
+            b = tuned[nb]
+            key = "levels=%d,P=%d,o=%d,%s" % (b.max_levels, b.patch, b.overlap,
+                                              "bf16" if b.ras_inverse == dcg.DCG_INV_BF16 else "fp32")
+            choices[key] = choices.get(key, 0) + 1
         probs.append(pr)
-        for r in range(nrhs):
+        fs.append(f0)
+        for r in range(1, nrhs):
             fs.append(torch.from_numpy(inputs.rhs(5, pr.N, p=p, r=r)).cuda())
+    torch.cuda.synchronize()
+    t_tune = time.perf_counter() - t_tune
     xs = [torch.zeros_like(f) for f in fs]
     # one outer iteration per problem, untimed: builds every W-cycle graph
     dcg.dcg_solve_batched(probs, 1, fs[::nrhs], xs[::nrhs], tol=1e-8, max_it=1)
@@ -521,7 +544,8 @@ def batched_extra(args, opts, dcg, inputs, torch):
            "batched_s": t_batched, "sequential_s": t_seq, "speedup": t_seq / t_batched,
            "batched_unknowns_per_s": unknowns / t_batched,
            "all_converged": code == dcg.DCG_OK and all(st["true_relres"] <= 1e-8 for st in stats),
-           "same_iterations_as_sequential": all(a["outer_its"] == b["outer_its"] for a, b in zip(stats, seq))}
+           "same_iterations_as_sequential": all(a["outer_its"] == b["outer_its"] for a, b in zip(stats, seq)),
+           "setup_and_autotune_s": t_tune, "autotuned_options_per_problem": choices or "not tuned"}
     for pr in probs:
         pr.close()
     return out
@@ -638,6 +662,7 @@ def main():
                     help="step sizes of the timed solves (default 1e-6 1e-5 1e-4); for profiling runs")
     ap.add_argument("--batched-problems", type=int, default=64)
     ap.add_argument("--batched-rhs", type=int, default=4)
+    ap.add_argument("--batched-no-tune", action="store_true")
     ap.add_argument("--levels", type=int, nargs="+", default=[2, 3, 4], help="hierarchy depths to autotune over")
     ap.add_argument("--ref-levels", type=int, default=2, help="hierarchy depth of the oracle in the reference arm")
     args = ap.parse_args()
