@@ -141,8 +141,9 @@ const char* dcg_last_error(void);
 int dcg_assemble(const dcg_mesh* mesh, double dt, double nu, const double* nu_elem,
                  int matrix_free, dcg_problem** out, void* stream);
 
-/* Build the inner hierarchy for `opts`: Z_J = V^T A V (checked on the device
- * to be the Q1 Laplacian stencil / d), Galerkin coarse stencils
+/* Build the inner hierarchy for `opts`: Z_J = V^T A V (read off the assembled
+ * matrix, or probed from the matrix-free operator, and checked on the device
+ * to be one constant stencil, the Q1 Laplacian / d), Galerkin coarse stencils
  * Z_{k-1} = P^T Z_k P (Algorithm 2 setup), RAS patch inverses (Section 4.2)
  * and the coarsest exact solver. May be called again with new options. */
 int dcg_setup(dcg_problem* p, const dcg_options* opts, void* stream);

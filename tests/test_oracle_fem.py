@@ -189,3 +189,27 @@ def test_spd():
     for d, n in [(2, 4), (3, 3)]:
         A = fem.assemble(d, n, 1e-6).matrix().toarray()
         assert np.linalg.eigvalsh(A).min() > 0
+
+
+def test_input_generators_follow_their_recipes():
+    """The seeded inputs: uniform[-1,1) right-hand sides, lognormal(0,1)
+    viscosities, batched sizes log-uniform in [64,512] rounded to multiples
+    of 16 and dt log-uniform in [1e-6,1e-1]; deterministic per seed."""
+    from paper_2606_13429_gb300 import inputs
+    f = inputs.rhs(3, 200_000)
+    assert f.min() >= -1.0 and f.max() < 1.0
+    assert abs(f.mean()) < 0.01 and abs(f.var() - 1.0 / 3.0) < 0.01
+    assert np.array_equal(f, inputs.rhs(3, 200_000)) and not np.array_equal(f, inputs.rhs(4, 200_000))
+    assert not np.array_equal(inputs.rhs(3, 1000, p=1), inputs.rhs(3, 1000, p=2))
+    nu = inputs.nu_elements(4, 200_000)
+    g = np.log(nu)
+    assert abs(g.mean()) < 0.01 and abs(g.std() - 1.0) < 0.01
+    plist = inputs.batched_problems(11, 4096)
+    ns = np.array([n for n, _ in plist])
+    dts = np.array([dt for _, dt in plist])
+    assert ns.min() >= 64 and ns.max() <= 512 and np.all(ns % 16 == 0)
+    assert dts.min() >= 1e-6 and dts.max() <= 1e-1
+    # log-uniform: log10(dt) spread evenly over [-6, -1]
+    h, _ = np.histogram(np.log10(dts), bins=5, range=(-6, -1))
+    assert h.min() > 0.15 * len(dts)
+    assert abs(np.mean(np.log(ns)) - (math.log(64) + math.log(512)) / 2) < 0.05
