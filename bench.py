@@ -326,6 +326,24 @@ def run_ours(args):
             extra["per_dt"].setdefault(str(dt), {})["plain_cg"] = {
                 "s": time.perf_counter() - t0, "outer_its": st["outer_its"], "true_relres": st["true_relres"]}
             pc.close()
+    if args.dcg_sweep:
+        # deflated CG at the large step sizes (thousands of outer iterations;
+        # not part of the default run)
+        sweep_opts = dcg.options(**{k: getattr(opts, k) for k, _ in opts._fields_})
+        sweep_opts.c = args.sweep_c if args.sweep_c else opts.c
+        for dt in [d for d in DTS_CG if d not in DTS]:
+            pd = dcg.dcg_assemble(2, n, dt)
+            dcg.dcg_setup(pd, sweep_opts)
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = dcg.dcg_solve(pd, f, x, tol=1e-8, max_it=args.max_it)
+            torch.cuda.synchronize()
+            extra["per_dt"].setdefault(str(dt), {})["dcg"] = {
+                "s": time.perf_counter() - t0, "outer_its": st["outer_its"], "total_mg_cycles": st["total_mg_cycles"],
+                "restarts": st["restarts"], "true_relres": st["true_relres"], "status": st["status"],
+                "c_F": sweep_opts.c}
+            pd.close()
     for dt, st in timed:
         extra["per_dt"].setdefault(str(dt), {})["dcg"] = {
             "s": st["solve_ms"] / 1e3, "outer_its": st["outer_its"], "total_mg_cycles": st["total_mg_cycles"],
@@ -658,6 +676,8 @@ def main():
     ap.add_argument("--skip-mf", action="store_true")
     ap.add_argument("--skip-mf-solve", action="store_true")
     ap.add_argument("--skip-3d", action="store_true")
+    ap.add_argument("--dcg-sweep", action="store_true", help="also time deflated CG at dt 1e-3..1e-1")
+    ap.add_argument("--sweep-c", type=float, default=None, help="inner tolerance factor c_F of that sweep")
     ap.add_argument("--dts", type=float, nargs="+", default=None,
                     help="step sizes of the timed solves (default 1e-6 1e-5 1e-4); for profiling runs")
     ap.add_argument("--batched-problems", type=int, default=64)

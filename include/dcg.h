@@ -108,7 +108,7 @@ typedef struct {
   int fcg_max_dirs;  /* FCG(inf): directions kept; 0 = up to max_it [0] */
   int check_every;   /* outer iterations between host convergence reads [1] */
   int stall_window;  /* deflated CG: a pass whose recursive residual has not
-                        fallen below 0.9 x its best value for
+                        fallen below 0.99 x its best value for
                         max(stall_window, its/4) iterations ends, is
                         reconstructed and restarted from its true residual
                         (such restarts do not count against max_restarts);

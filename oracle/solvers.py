@@ -157,7 +157,7 @@ class FDCG:
         rr = r @ r
         its = 0
         conv = np.sqrt(rr) <= eps
-        # stall test: the recursive residual has not fallen below 0.9 x its
+        # stall test: the recursive residual has not fallen below 0.99 x its
         # best value for max(stall_window, its/4) iterations
         stalled = False
         best, its_best = np.sqrt(rr), 0
@@ -178,7 +178,7 @@ class FDCG:
             if np.sqrt(rr_new) <= eps:
                 conv = True
                 break
-            if np.sqrt(rr_new) < 0.9 * best:
+            if np.sqrt(rr_new) < 0.99 * best:
                 best, its_best = np.sqrt(rr_new), its
             elif o.stall_window > 0 and its - its_best > max(o.stall_window, its // 4):
                 stalled = True

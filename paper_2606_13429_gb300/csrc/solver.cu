@@ -159,7 +159,7 @@ int pi_of_Ax(Ctx& c, const double* x, double* z, double tc, bool in_iter) {
 }
 
 // One pass of Algorithm 2 from x0 (or zero). *stalled is set when the pass
-// ended because its recursive residual stopped falling (no value below 0.9 x
+// ended because its recursive residual stopped falling (no value below 0.99 x
 // the best one for max(stall_window, its/4) iterations): the recursion of an
 // inexactly projected operator can lose orthogonality at large dt, and the
 // caller then restarts from the true residual of the reconstructed iterate.
@@ -252,7 +252,7 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged, 
       break;
     }
     ++its;
-    if (std::sqrt(rrn) < 0.9 * best) {
+    if (std::sqrt(rrn) < 0.99 * best) {
       best = std::sqrt(rrn);
       its_best = its;
     } else if (window > 0 && its - its_best > std::max(window, its / 4)) {
