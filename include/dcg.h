@@ -112,7 +112,7 @@ typedef struct {
                         max(stall_window, its/4) iterations ends, is
                         reconstructed and restarted from its true residual
                         (such restarts do not count against max_restarts);
-                        0 = off [50] */
+                        0 = off [200] */
 } dcg_options;
 
 typedef struct {

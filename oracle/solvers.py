@@ -96,7 +96,7 @@ class FDCGOptions:
     inner_nmax: int = 100
     recurrence: str = "fcg1"       # "fcg1" | "fr" | "fcg_inf"
     max_restarts: int = 3
-    stall_window: int = 50         # restart a pass whose residual stopped falling; 0 = off
+    stall_window: int = 200        # restart a pass whose residual stopped falling; 0 = off
 
 
 class FDCG:

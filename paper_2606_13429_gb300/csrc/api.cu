@@ -165,7 +165,7 @@ void dcg_default_options(dcg_options* o) {
   o->max_restarts = 3;
   o->fcg_max_dirs = 0;
   o->check_every = 1;
-  o->stall_window = 50;
+  o->stall_window = 200;
 }
 
 const char* dcg_status_string(int s) {

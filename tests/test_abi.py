@@ -38,7 +38,7 @@ def test_default_options(lib):
     assert (o.max_levels, o.patch, o.overlap, o.m1, o.m2) == (4, 4, 1, 2, 2)
     assert o.inner_rule == dcg.DCG_INNER_FIXED and abs(o.c - 0.01) < 1e-15
     assert o.recurrence == dcg.DCG_FCG1 and o.precision == dcg.DCG_FP64 and o.deflate == 1
-    assert o.inner_nmax == 100 and o.max_restarts == 3 and o.check_every == 1 and o.stall_window == 50
+    assert o.inner_nmax == 100 and o.max_restarts == 3 and o.check_every == 1 and o.stall_window == 200
 
 
 def test_status_strings(lib):
