@@ -150,7 +150,10 @@ int dcg_setup(dcg_problem* p, const dcg_options* opts, void* stream);
 
 /* Solve A x = f to ||f - A x|| <= tol ||f|| (true residual, FP64).
  * f_dev, x_dev: device arrays of N doubles; x_dev holds the initial guess on
- * entry and the solution on exit. Returns DCG_OK, DCG_ERR_NOT_CONVERGED or
+ * entry and the solution on exit. A deflated pass that ends above tol (its
+ * recursion converged, or stalled: see dcg_options.stall_window) is
+ * reconstructed and the solve continues from its true residual
+ * (stats.restarts counts these). Returns DCG_OK, DCG_ERR_NOT_CONVERGED or
  * DCG_ERR_BREAKDOWN (stats filled in all three cases), or an error. */
 int dcg_solve(dcg_problem* p, const double* f_dev, double* x_dev, double tol,
               int max_it, dcg_stats* stats, void* stream);
@@ -227,7 +230,9 @@ int dcg_inner_apply(const dcg_problem* p, const double* z_dev, double* y_dev, vo
  * `ncycles` times (z in/out, FP64, n_nodes), in the precision set up. */
 int dcg_mg_cycles(dcg_problem* p, const double* g_dev, double* z_dev, int ncycles, void* stream);
 
-/* Algorithm 3: cycles until ||g - Z_J z|| <= tol ||g|| or nmax; *ncycles out. */
+/* Algorithm 3: cycles until ||g - Z_J z|| <= tol ||g|| or nmax; *ncycles out.
+ * The residual is formed in FP64; with an FP32 cycle its norm (which only
+ * feeds this test) is summed from the FP32 copy the cycle receives. */
 int dcg_mg_solve(dcg_problem* p, const double* g_dev, double* z_dev, double tol, int nmax,
                  int* ncycles, void* stream);
 
@@ -240,7 +245,7 @@ int dcg_ras_step(dcg_problem* p, int level, const double* f_dev, double* z_dev, 
 int dcg_coarse_solve(dcg_problem* p, const double* f_dev, double* z_dev, void* stream);
 
 /* ---- timing of kernel classes (CUDA events, off by default) ----------- */
-#define DCG_PROF_SPMV        0  /* BSR products (all fused variants) */
+#define DCG_PROF_SPMV        0  /* operator products (fused BSR variants, matrix-free) */
 #define DCG_PROF_VEC         1  /* vector updates and reductions */
 #define DCG_PROF_RAS_SOLVE   2  /* RAS residual + shared-inverse products */
 #define DCG_PROF_RAS_UPDATE  3  /* RAS weighted combination */
