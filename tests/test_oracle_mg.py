@@ -8,6 +8,7 @@ import pytest
 import scipy.sparse as sp
 
 from oracle import fem, mg
+from paper_2606_13429_gb300 import inputs
 
 
 def _hier(d, n, **kw):
@@ -170,3 +171,32 @@ def test_multigrid_driver_counts():
     zb, nb = H.multigrid(f, 1e-10, n - 1)
     assert nb == n - 1
     assert np.linalg.norm(f - Z @ zb) > 1e-10 * np.linalg.norm(f)
+
+
+def test_coarsest_wcycle_ignores_its_initial_guess():
+    """On the coarsest level Algorithm 4's W is the exact solve, so its second
+    recursive call W_1(r_c, e1) returns the same vector as the first, W_1(r_c, 0):
+    a two-level W-cycle equals one that solves the coarse problem once."""
+    d, n = 2, 16
+    asm = fem.assemble(d, n, 1e-3)
+    V = fem.V_matrix(asm.mesh)
+    H = mg.Hierarchy(d, n, mg.inner_matrix(V, asm.matrix()),
+                     mg.MGOptions(patch=4, overlap=1, max_levels=2))
+    assert H.J == 2
+    rc = inputs.rhs(1, H.levels[0].Z.shape[0])
+    e1 = H.wcycle(rc, np.zeros_like(rc), 1)
+    e2 = H.wcycle(rc, e1, 1)
+    assert np.array_equal(e1, e2)
+    assert np.array_equal(e1, H.wcycle(rc, inputs.rhs(2, rc.size), 1))
+    # and the full two-level cycle with one coarse solve gives the same result
+    f = inputs.rhs(3, H.levels[1].Z.shape[0])
+    z_ref = H.wcycle(f, np.zeros_like(f))
+    lev = H.levels[1]
+    z = np.zeros_like(f)
+    for _ in range(H.opts.m1):
+        z = H.ras_step(2, f, z)
+    rc2 = H.restrict(2, f - lev.Z @ z)
+    z = z + H.prolong(2, H.coarse_solve(rc2))
+    for _ in range(H.opts.m2):
+        z = H.ras_step(2, f, z)
+    assert np.array_equal(z, z_ref)
