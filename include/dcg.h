@@ -190,7 +190,9 @@ int dcg_solve_batched(int nprob, dcg_problem* const* probs, int nrhs,
  * The fastest candidate wins; candidates that fail to reach inner_tol are
  * skipped. On return the problem is set up with the winner, *best holds it
  * and *best_ms its time per inner solve. f_dev: device array of N (a
- * representative right-hand side). Temporary device memory: 2 n_nodes doubles. */
+ * representative right-hand side). Temporary device memory: 2 n_nodes doubles.
+ * On an error return the problem may be left set up with the candidate that
+ * was being tried, or not set up (DCG_ERR_STATE on solve): set it up again. */
 int dcg_autotune(dcg_problem* p, const dcg_options* base, const double* f_dev, double inner_tol,
                  int reps, dcg_options* best, double* best_ms, void* stream);
 
