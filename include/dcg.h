@@ -55,7 +55,8 @@ extern "C" {
 #define DCG_OK                 0
 #define DCG_ERR_INVALID_ARG    1  /* n < 2, dt <= 0, nu <= 0, tol <= 0, NULL, bad option */
 #define DCG_ERR_NOT_CONVERGED  2  /* max_it reached; x holds the last iterate, stats filled */
-#define DCG_ERR_BREAKDOWN      3  /* (d, M_D d) <= 0 or non-finite; x holds the last iterate */
+#define DCG_ERR_BREAKDOWN      3  /* (d, M_D d) <= 0 or non-finite (also a non-finite
+                                     right-hand side or initial guess); x holds the last iterate */
 #define DCG_ERR_CUDA           4  /* a CUDA call failed; see dcg_last_error() */
 #define DCG_ERR_OOM            5  /* device allocation failed */
 #define DCG_ERR_UNSUPPORTED    6  /* configuration outside what the kernels implement */
@@ -68,7 +69,9 @@ extern "C" {
 
 #define DCG_FCG1     0  /* flexible CG truncated to one direction (m_i = 1) */
 #define DCG_FR       1  /* classical CG coefficients on the deflated system */
-#define DCG_FCG_INF  2  /* untruncated FCG (Algorithm 1), directions stored */
+#define DCG_FCG_INF  2  /* FCG of Algorithm 1 with directions stored; untruncated while a
+                           pass has at most fcg_max_dirs iterations, then the
+                           truncation-restart rule of the remark after Table 4 */
 
 #define DCG_FP64   0  /* everything in FP64 */
 #define DCG_MIXED  1  /* W-cycle (stencils, transfers, RAS) in FP32; outer CG FP64 */
@@ -105,8 +108,15 @@ typedef struct {
   int ras_weights;   /* DCG_RAS_* [MULTIPLICITY] */
   int deflate;       /* 1 = deflated CG, 0 = plain CG [1] */
   int max_restarts;  /* true-residual restarts after reconstruction [3] */
-  int fcg_max_dirs;  /* FCG(inf): directions kept; 0 = up to max_it [0] */
-  int check_every;   /* outer iterations between host convergence reads [1] */
+  int fcg_max_dirs;  /* DCG_FCG_INF: m_max of the truncation-restart rule
+                        m_i = max{1, mod(i, m_max + 1)} (remark after Table 4):
+                        direction d_i is orthogonalised against the m_i most
+                        recent directions, so a pass of at most m_max
+                        iterations is the untruncated FCG(inf). Directions
+                        d and M_D d are kept in 2 * m_max device vectors of N
+                        doubles. 0 = min(256, the count that fits 8 GiB) [0] */
+  int check_every;   /* plain CG only: iterations between host convergence
+                        reads (deflated CG reads every iteration) [1] */
   int stall_window;  /* deflated CG: a pass whose recursive residual has not
                         fallen below 0.99 x its best value for
                         max(stall_window, its/4) iterations ends, is
@@ -124,6 +134,8 @@ typedef struct {
   double avg_inner;      /* iter_mg_cycles / outer_its (paper's "Inn") */
   double true_relres;    /* ||f - A x||_2 / ||f||_2 in FP64 */
   double solve_ms;       /* wall time of the solve on the stream */
+  int fcg_truncated;     /* DCG_FCG_INF: directions built from fewer than all
+                            previous ones of their pass (m_i < i) */
 } dcg_stats;
 
 void dcg_default_options(dcg_options* opts);
@@ -203,6 +215,10 @@ void dcg_destroy(dcg_problem* p);
 /* Sizes: N unknowns, interior nodes, stored blocks, multigrid levels. */
 int dcg_problem_info(const dcg_problem* p, long long* n_unknowns, long long* n_nodes,
                      long long* nnzb, int* levels);
+
+/* Interior nodes of multigrid level `level` (1 = coarsest, levels = finest,
+ * the inner system of Algorithm 2) after dcg_setup; DCG_ERR_STATE before. */
+int dcg_level_nodes(const dcg_problem* p, int level, long long* nodes);
 
 /* Copy the BSR pattern / values to host arrays of n_nodes+1, nnzb and
  * nnzb*b*b entries (synchronous). */
@@ -287,6 +303,23 @@ int dcg_profile_read(dcg_problem* p, int cls, double* ms, long long* launches, d
  * overlaps on the GPU race and must be serialised by the caller. */
 #define DCG_STATIC_COARSE_MAX 131072
 int dcg_coarse_solve_static(dcg_problem* p, const double* f_dev, double* z_dev, void* stream);
+
+/* ---- diagnostics (no counterpart in the paper) -------------------------- */
+
+/* Arithmetic rate of this GPU's FMA pipes as the library's kernels see
+ * them, measured with independent FMA chains on all SMs (no memory
+ * traffic): precision DCG_FP64 for FP64 FMAs, DCG_MIXED for FP32 FMAs.
+ * *tflops = 2 x FMAs per second / 1e12, best of three timed launches
+ * (about 20 ms of GPU time each; synchronises `stream`). It is the ALU peak
+ * the rooflines of the FP64-bound kernels are quoted against. */
+int dcg_measure_fma_rate(int precision, double* tflops, void* stream);
+
+/* Self-test of the bounded mbarrier wait that every bulk-copy kernel uses:
+ * one CTA waits, with a limit of max_polls polls, on an mbarrier that nothing
+ * will complete (no copy is in flight), records that the wait gave up and
+ * returns normally. *gave_up = 1 when the wait gave up as designed; the CUDA
+ * context stays usable. Synchronises `stream`. */
+int dcg_selftest_bounded_wait(unsigned max_polls, int* gave_up, void* stream);
 
 /* Number of kernels this library has launched in the process so far (a
  * replay of the captured W-cycle graph counts each of its kernel nodes). */

@@ -21,14 +21,24 @@ FDCG follows Algorithm 2 with the outer FCG of Algorithm 1:
 Recurrences (Algorithm 1; truncation rule of the FCG remark):
 * "fcg1": m_i = 1, d_i = r_i - beta d_{i-1}, beta = (r_i, q_{i-1})/(d_{i-1}, q_{i-1}),
   alpha = (d_i, r_i)/(d_i, q_i) with q = M_D(d).
-* "fcg_inf": d_i orthogonalised against every previous direction, q_k stored
-  when computed (Notay's variant; the paper re-applies A*(d_k, tol)).
+* "fcg_inf": with m_max = None, d_i orthogonalised against every previous
+  direction (Algorithm 1 as printed), q_k stored when computed (Notay's
+  variant; the paper re-applies A*(d_k, tol)). With an integer m_max, the
+  mixed truncation-restart rule of the remark after Table 4: m_0 = 0,
+  m_i = max{1, mod(i, m_max + 1)}, and d_i is orthogonalised against the
+  m_i most recent directions d_{i-m_i}, ..., d_{i-1} only. m_max = 0 gives
+  FCG(1); m_max at least the iteration count gives the untruncated method.
 * "fr": classical CG coefficients, alpha = (r,r)/(d,q), beta = (r',r')/(r,r).
 
 Reading (not in the paper): after reconstruction the true residual
 ||f - A x|| / ||f|| is computed in FP64; if it is above tol, the same FDCG is
 run on the residual equation A e = f - A x (same absolute threshold
 tol ||f||) and x += e, at most ``max_restarts`` times.
+
+Optional stall restart (not in the paper, off unless ``stall_window`` > 0):
+a pass whose recursive residual has not fallen below 0.99 x its best value
+for max(stall_window, its/4) iterations ends, is reconstructed, and the
+solve continues from its true residual like the restart above.
 """
 from __future__ import annotations
 
@@ -49,7 +59,9 @@ class SolveStats:
     true_relres: float = float("nan")
     converged: bool = False
     breakdown: bool = False
-    history: list = field(default_factory=list)
+    history: list = field(default_factory=list)    # ||r_{i+1}|| after each outer iteration
+    res0: list = field(default_factory=list)       # ||r_0|| of each pass
+    inner_tols: list = field(default_factory=list)  # tau_c passed to Multigrid in M_D, per outer iteration
 
     @property
     def avg_inner(self) -> float:
@@ -95,8 +107,9 @@ class FDCGOptions:
     c: float = 0.01                # c_F or c_A
     inner_nmax: int = 100
     recurrence: str = "fcg1"       # "fcg1" | "fr" | "fcg_inf"
+    m_max: int | None = None       # fcg_inf: truncation-restart parameter (None = untruncated)
     max_restarts: int = 3
-    stall_window: int = 200        # restart a pass whose residual stopped falling; 0 = off
+    stall_window: int = 0          # restart a pass whose residual stopped falling; 0 = off
 
 
 class FDCG:
@@ -161,8 +174,10 @@ class FDCG:
         # best value for max(stall_window, its/4) iterations
         stalled = False
         best, its_best = np.sqrt(rr), 0
+        st.res0.append(np.sqrt(rr))
         while not conv and st.outer_its < max_it:
             tc = self._inner_tol(np.sqrt(rr), eps, tol)
+            st.inner_tols.append(tc)
             q = self.M_D(d, tc, st)
             dq = d @ q
             if not (dq > 0.0) or not np.isfinite(dq):
@@ -188,12 +203,15 @@ class FDCG:
             elif o.recurrence == "fcg1":
                 d = r - ((r @ q) / dq) * d
             elif o.recurrence == "fcg_inf":
+                # d_{i} for i = len(dirs) + 1 directions stored so far
                 dirs.append(d)
                 qs.append(q)
                 dqs.append(dq)
+                i = len(dirs)
+                mi = i if o.m_max is None else max(1, i % (o.m_max + 1))
                 dn = r.copy()
-                for dk, qk, dqk in zip(dirs, qs, dqs):
-                    dn = dn - ((r @ qk) / dqk) * dk
+                for k in range(i - mi, i):
+                    dn = dn - ((r @ qs[k]) / dqs[k]) * dirs[k]
                 d = dn
             else:
                 raise ValueError(o.recurrence)

@@ -55,8 +55,9 @@ int check_options(const dcg_options* o, int dim) {
 
 void free_solver_buffers(dcg_problem* p) {
   SolverBuffers& b = p->sb;
-  double* all[] = {b.xh, b.r, b.d, b.q, b.u, b.e, b.g, b.zh, b.zf, b.rin, b.dirs, b.qdirs, b.coef, b.w};
+  double* all[] = {b.xh, b.r, b.d, b.q, b.u, b.e, b.g, b.zh, b.zf, b.rin, b.dirs, b.qdirs, b.dqs, b.coef, b.part, b.w};
   for (double* v : all) cudaFree(v);
+  cudaFree(b.ndir_dev);
   b = SolverBuffers{};
 }
 
@@ -280,7 +281,10 @@ int dcg_setup(dcg_problem* p, const dcg_options* opts, void* stream) {
       b.ndir_cap = (int)cap;
       DCG_TRY(alloc_vec(&b.dirs, cap * N));
       DCG_TRY(alloc_vec(&b.qdirs, cap * N));
-      DCG_TRY(alloc_vec(&b.coef, 2 * cap));
+      DCG_TRY(alloc_vec(&b.dqs, cap));
+      DCG_TRY(alloc_vec(&b.coef, cap));
+      DCG_TRY(alloc_vec(&b.part, cap * 2 * 152));
+      DCG_CUDA(cudaMalloc(&b.ndir_dev, sizeof(int)));
     }
     DCG_TRY(mg_setup(p, s));
   }
@@ -514,6 +518,17 @@ int dcg_problem_info(const dcg_problem* p, long long* n_unknowns, long long* n_n
   if (n_nodes) *n_nodes = p->n_nodes;
   if (nnzb) *nnzb = p->matrix_free ? 0 : p->nnzb;
   if (levels) *levels = (int)p->levels.size();
+  return DCG_OK;
+}
+
+int dcg_level_nodes(const dcg_problem* p, int level, long long* nodes) {
+  if (!p || !nodes) return DCG_ERR_INVALID_ARG;
+  if (!p->is_setup || p->levels.empty()) return DCG_ERR_STATE;
+  if (level < 1 || level > (int)p->levels.size()) {
+    set_error_msg("dcg_level_nodes: level out of range");
+    return DCG_ERR_INVALID_ARG;
+  }
+  *nodes = p->levels[level - 1].nn;
   return DCG_OK;
 }
 

@@ -206,9 +206,13 @@ struct SolverBuffers {
   double *xh = nullptr, *r = nullptr, *d = nullptr, *q = nullptr, *u = nullptr, *e = nullptr;
   double *g = nullptr, *zh = nullptr, *zf = nullptr, *rin = nullptr;  // inner FP64 (n_nodes)
   double* w = nullptr;     // operand d - V zh of the deflated product (assembled A)
-  double* dirs = nullptr;  // FCG(inf): [ndir][N] directions
-  double* qdirs = nullptr; // FCG(inf): [ndir][N] M_D directions
-  double* coef = nullptr;  // FCG(inf): [ndir] coefficients
+  // FCG(inf) with the truncation-restart rule: ring of ndir_cap = m_max slots
+  double* dirs = nullptr;  // [m_max][N] directions d_k (slot k mod m_max)
+  double* qdirs = nullptr; // [m_max][N] q_k = M_D d_k
+  double* dqs = nullptr;   // [m_max] (d_k, q_k)
+  double* coef = nullptr;  // [m_max] (r_i, q_k) of the current window
+  double* part = nullptr;  // [m_max * 304] per-CTA partial sums of the window's dot products
+  int* ndir_dev = nullptr; // directions stored in the current pass (device counter)
   int ndir_cap = 0;
 };
 

@@ -1884,7 +1884,9 @@ namespace dcg {
 namespace {
 static __device__ __align__(256) double g_static_coarse_tmp[DCG_STATIC_COARSE_MAX];
 constexpr int kMaxDevices = 64;
-double* g_static_coarse_ptr[kMaxDevices] = {};
+// per-device address of the array, looked up on the first call with that
+// device current; atomic, so first calls from several host threads are safe
+std::atomic<double*> g_static_coarse_ptr[kMaxDevices] = {};
 }  // namespace
 }  // namespace dcg
 
@@ -1916,12 +1918,13 @@ extern "C" int dcg_coarse_solve_static(dcg_problem* p, const double* f_dev, doub
     set_error_msg("dcg_coarse_solve_static: device index out of range");
     return DCG_ERR_UNSUPPORTED;
   }
-  if (!g_static_coarse_ptr[dev]) {
+  double* tmp = g_static_coarse_ptr[dev].load(std::memory_order_acquire);
+  if (!tmp) {
     void* ptr = nullptr;
     DCG_CUDA(cudaGetSymbolAddress(&ptr, g_static_coarse_tmp));
-    g_static_coarse_ptr[dev] = static_cast<double*>(ptr);
+    tmp = static_cast<double*>(ptr);
+    g_static_coarse_ptr[dev].store(tmp, std::memory_order_release);  // every thread finds the same address
   }
-  double* tmp = g_static_coarse_ptr[dev];
   cudaStream_t s = (cudaStream_t)stream;
   const int nl = D == 2 ? fdm_passes<double, 2>(f_dev, z_dev, tmp, C.S64, C.lam64, C.tw64, C.log2n2, C.m, s)
                         : fdm_passes<double, 3>(f_dev, z_dev, tmp, C.S64, C.lam64, C.tw64, C.log2n2, C.m, s);

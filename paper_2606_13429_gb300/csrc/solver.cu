@@ -75,17 +75,95 @@ __global__ void k_direction(double* __restrict__ d, const double* __restrict__ r
 // after k_direction has read both: S_RR <- S_RRN
 __global__ void k_roll(double* sc) { sc[S_RR] = sc[S_RRN]; }
 
-// FCG(inf): d = r - sum_k (c_k / dq_k) d_k
-__global__ void k_orth_direction(double* __restrict__ d, const double* __restrict__ r, const double* __restrict__ dirs,
-                                 const double* __restrict__ coef, const double* __restrict__ dqs, int K, long long n,
-                                 Reduce red) {
-  double part[1] = {0.0};
+// FCG with the truncation-restart rule of the remark after Table 4: the
+// direction d_i (i = number of directions stored so far, ndir[0]) is
+// orthogonalised against the m_i = max{1, mod(i, m_max + 1)} most recent
+// ones, d_{i-m_i} .. d_{i-1}, kept in a ring of m_max slots (direction k in
+// slot k mod m_max). m_max at least the iteration count is Algorithm 1's
+// untruncated FCG(inf); m_max = 0 would be FCG(1), which has its own kernels.
+__device__ __forceinline__ int fcg_window(int i, int cap) {
+  const int mi = max(1, i % (cap + 1));
+  return min(mi, i);
+}
+
+// slot of d_i: d, q and (d, q) copied into the ring; ndir[0] += 1
+__global__ void k_store_dir(const double* __restrict__ d, const double* __restrict__ q, double* __restrict__ dirs,
+                            double* __restrict__ qdirs, const int* __restrict__ ndir, int cap, long long n) {
+  const int slot = ndir[0] % cap;
+  double* ds = dirs + (size_t)slot * n;
+  double* qs = qdirs + (size_t)slot * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double ri = r[i];
-    double di = ri;
-    for (int k = 0; k < K; ++k) di = fma(-(coef[k] / dqs[k]), dirs[(size_t)k * n + i], di);
-    d[i] = di;
-    part[0] = fma(di, ri, part[0]);
+    ds[i] = d[i];
+    qs[i] = q[i];
+  }
+}
+__global__ void k_store_dq(double* __restrict__ dqs, const double* __restrict__ sc, int* __restrict__ ndir, int cap) {
+  dqs[ndir[0] % cap] = sc[S_DQ];
+  ndir[0] += 1;
+}
+
+// c_j = (r, q_{first + j}) for the window of d_i: one pass over r per group
+// of kMultiDot directions (blockIdx.y); per-CTA partial sums go to
+// part[j * gridDim.x + blockIdx.x] and k_multi_dot_finish adds them in block
+// order (deterministic).
+constexpr int kMultiDot = 8;
+constexpr int kMultiDotGrid = 2 * 152;  // CTAs along the vector (partials per direction)
+__global__ void __launch_bounds__(kRedThreads) k_multi_dot(const double* __restrict__ r, const double* __restrict__ qdirs,
+                                                            const int* __restrict__ ndir, int cap, long long n,
+                                                            double* __restrict__ part) {
+  __shared__ double smem[32 * kMultiDot];
+  const int i = ndir[0];
+  const int K = fcg_window(i, cap), first = i - K;
+  const int j0 = blockIdx.y * kMultiDot;
+  if (j0 >= K) return;  // uniform per CTA
+  const double* qk[kMultiDot];
+#pragma unroll
+  for (int j = 0; j < kMultiDot; ++j) qk[j] = qdirs + (size_t)((first + min(j0 + j, K - 1)) % cap) * n;
+  double acc[kMultiDot];
+#pragma unroll
+  for (int j = 0; j < kMultiDot; ++j) acc[j] = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double rt = r[t];
+#pragma unroll
+    for (int j = 0; j < kMultiDot; ++j) acc[j] = fma(rt, __ldg(qk[j] + t), acc[j]);
+  }
+  block_sum<kMultiDot>(acc, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < kMultiDot; ++j)
+      if (j0 + j < K) part[(size_t)(j0 + j) * gridDim.x + blockIdx.x] = acc[j];
+  }
+}
+
+// coef[j] = sum over CTAs of part[j][.] (one CTA per window entry)
+__global__ void k_multi_dot_finish(const double* __restrict__ part, int nbx, const int* __restrict__ ndir, int cap,
+                                   double* __restrict__ coef) {
+  __shared__ double smem[32];
+  const int K = fcg_window(ndir[0], cap);
+  const int j = blockIdx.x;
+  if (j >= K) return;
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < nbx; b += blockDim.x) v[0] += part[(size_t)j * nbx + b];
+  block_sum<1>(v, smem);
+  if (threadIdx.x == 0) coef[j] = v[0];
+}
+
+// d_i = r - sum_j (c_j / dq_{first+j}) d_{first+j}; (d_i, r) -> red
+__global__ void k_orth_direction(double* __restrict__ d, const double* __restrict__ r, const double* __restrict__ dirs,
+                                 const double* __restrict__ coef, const double* __restrict__ dqs,
+                                 const int* __restrict__ ndir, int cap, long long n, Reduce red) {
+  const int i = ndir[0];
+  const int K = fcg_window(i, cap), first = i - K;
+  double part[1] = {0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double rt = r[t];
+    double dt = rt;
+    for (int j = 0; j < K; ++j) {
+      const int sl = (first + j) % cap;
+      dt = fma(-(coef[j] / dqs[sl]), dirs[(size_t)sl * n + t], dt);
+    }
+    d[t] = dt;
+    part[0] = fma(dt, rt, part[0]);
   }
   grid_reduce<1>(part, red);
 }
@@ -199,6 +277,7 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged, 
   if (std::sqrt(rr) <= c.eps) *converged = true;
   const bool fcginf = c.rule == R_FCGINF;
   int ndir = 0;
+  if (fcginf) DCG_CUDA(cudaMemsetAsync(b.ndir_dev, 0, sizeof(int), s));
   *stalled = false;
   const int window = p->opts.stall_window;
   double best = std::sqrt(rr);
@@ -219,11 +298,13 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged, 
       DCG_TRY(spmv_defl(p, b.d, b.zh, b.q, S_DQ, s, mf_lowp(p)));
     }
     if (fcginf) {
-      // store d_k, q_k before the update (ring buffer of ndir_cap)
-      const int slot = ndir % b.ndir_cap;
-      DCG_TRY(vec_copy(b.dirs + (size_t)slot * N, b.d, N, s));
-      DCG_TRY(vec_copy(b.qdirs + (size_t)slot * N, b.q, N, s));
-      DCG_CUDA(cudaMemcpyAsync(b.coef + b.ndir_cap + slot, p->scal + S_DQ, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      // d_{i-1}, q_{i-1} and their product into the ring before the update
+      const int prof2 = prof_begin(p, PC_VEC, s);
+      k_store_dir<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.q, b.dirs, b.qdirs, b.ndir_dev, b.ndir_cap, N);
+      DCG_LAUNCH_CHECK();
+      k_store_dq<<<1, 1, 0, s>>>(b.dqs, p->scal, b.ndir_dev, b.ndir_cap);
+      DCG_LAUNCH_CHECK();
+      prof_end(p, prof2, s, 0.0, 32.0 * N);
       ++ndir;
     }
     int prof = prof_begin(p, PC_VEC, s);
@@ -260,16 +341,21 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged, 
       break;
     }
     if (fcginf) {
-      const int K = ndir < b.ndir_cap ? ndir : b.ndir_cap;
-      for (int k = 0; k < K; ++k) {
-        const double* qk = b.qdirs + (size_t)k * N;
-        // c_k = r . q_k
-        DCG_TRY(vec_dot(p, b.r, qk, N, S_TMP0, s));
-        DCG_CUDA(cudaMemcpyAsync(b.coef + k, p->scal + S_TMP0, sizeof(double), cudaMemcpyDeviceToDevice, s));
-      }
-      k_orth_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, b.dirs, b.coef, b.coef + b.ndir_cap, K, N,
-                                                          make_reduce(p, S_DR));
+      // window of the truncation-restart rule (host mirror of ndir, for the
+      // launch shape and the statistics only)
+      const int mi = std::max(1, ndir % (b.ndir_cap + 1));
+      const int K = std::min(mi, ndir);
+      if (K < ndir) c.st->fcg_truncated++;
+      const int gy = (K + 7) / 8;
+      const int prof2 = prof_begin(p, PC_VEC, s);
+      k_multi_dot<<<dim3(kMultiDotGrid, gy), kRedThreads, 0, s>>>(b.r, b.qdirs, b.ndir_dev, b.ndir_cap, N, b.part);
       DCG_LAUNCH_CHECK();
+      k_multi_dot_finish<<<K, kRedThreads, 0, s>>>(b.part, kMultiDotGrid, b.ndir_dev, b.ndir_cap, b.coef);
+      DCG_LAUNCH_CHECK();
+      k_orth_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, b.dirs, b.coef, b.dqs, b.ndir_dev, b.ndir_cap,
+                                                          N, make_reduce(p, S_DR));
+      DCG_LAUNCH_CHECK();
+      prof_end(p, prof2, s, 4.0 * K * N, 8.0 * N * (2.0 * K + 2.0 + (double)gy));
     } else {
       prof = prof_begin(p, PC_VEC, s);
       k_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, N, p->scal, c.rule == R_FCG1, make_reduce(p, S_DR));
@@ -361,6 +447,14 @@ int solve_device(dcg_problem* p, const double* f, double* x, double tol, int max
   DCG_TRY(read_scalars(p, s));
   c.fnorm = std::sqrt(p->scal_host[S_FF]);
   const bool x0_nonzero = p->scal_host[S_TMP1] != 0.0;
+  if (!std::isfinite(c.fnorm) || !std::isfinite(p->scal_host[S_TMP1])) {
+    // a NaN or infinite entry in f or x0: no iteration can be formed
+    DCG_CUDA(cudaStreamSynchronize(s));
+    st->status = DCG_ERR_BREAKDOWN;
+    st->true_relres = std::nan("");
+    set_error_msg("dcg_solve: non-finite entries in the right-hand side or the initial guess");
+    return st->status;
+  }
   if (!(c.fnorm > 0.0)) {
     DCG_TRY(vec_zero(x, N, s));
     DCG_CUDA(cudaStreamSynchronize(s));

@@ -49,7 +49,7 @@ class dcg_options(C.Structure):
 class dcg_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_its", C.c_int), ("total_mg_cycles", C.c_int),
                 ("iter_mg_cycles", C.c_int), ("restarts", C.c_int), ("avg_inner", C.c_double),
-                ("true_relres", C.c_double), ("solve_ms", C.c_double)]
+                ("true_relres", C.c_double), ("solve_ms", C.c_double), ("fcg_truncated", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH):
         "dcg_solve_batched": (I, [I, C.POINTER(P), I, C.POINTER(VP), C.POINTER(VP), D, I, C.POINTER(dcg_stats), VP]),
         "dcg_destroy": (None, [P]),
         "dcg_problem_info": (I, [P, C.POINTER(LL), C.POINTER(LL), C.POINTER(LL), C.POINTER(I)]),
+        "dcg_level_nodes": (I, [P, I, C.POINTER(LL)]),
         "dcg_export_pattern": (I, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "dcg_export_values": (I, [P, C.POINTER(C.c_double)]),
         "dcg_spmv": (I, [P, VP, VP, VP]),
@@ -98,6 +99,8 @@ def load(path: str = LIB_PATH):
         "dcg_profile_enable": (I, [P, C.c_uint, VP]),
         "dcg_profile_read": (I, [P, I, C.POINTER(D), C.POINTER(LL), C.POINTER(D), C.POINTER(D), VP]),
         "dcg_kernel_launches": (LL, []),
+        "dcg_measure_fma_rate": (I, [I, C.POINTER(D), VP]),
+        "dcg_selftest_bounded_wait": (I, [C.c_uint, C.POINTER(I), VP]),
         "dcg_coarse_solve_static": (I, [P, VP, VP, VP]),
         "dcg_autotune": (I, [P, C.POINTER(dcg_options), VP, D, I, C.POINTER(dcg_options), C.POINTER(D), VP]),
     }
@@ -176,6 +179,12 @@ class Problem:
         lv = C.c_int()
         _check(load().dcg_problem_info(self.ptr, None, None, None, C.byref(lv)), "dcg_problem_info")
         return lv.value
+
+    def level_nodes(self, level: int) -> int:
+        """Interior nodes of multigrid level `level` (1 = coarsest)."""
+        nn = C.c_longlong()
+        _check(load().dcg_level_nodes(self.ptr, level, C.byref(nn)), "dcg_level_nodes")
+        return nn.value
 
     def close(self):
         if self.ptr and self.ptr.value:
@@ -322,12 +331,14 @@ def dcg_mg_solve(prob: Problem, g, z, tol, nmax=100, stream=None) -> int:
 
 
 def dcg_ras_step(prob: Problem, level, f, z, stream=None):
-    _check(load().dcg_ras_step(prob.ptr, level, _dptr(f, name="f"), _dptr(z, name="z"), _stream(stream)),
+    nn = prob.level_nodes(level) if 1 <= level <= prob.levels else None
+    _check(load().dcg_ras_step(prob.ptr, level, _dptr(f, nn, "f"), _dptr(z, nn, "z"), _stream(stream)),
            "dcg_ras_step")
 
 
 def dcg_coarse_solve(prob: Problem, f, z, stream=None):
-    _check(load().dcg_coarse_solve(prob.ptr, _dptr(f, name="f"), _dptr(z, name="z"), _stream(stream)),
+    nn = prob.level_nodes(1)
+    _check(load().dcg_coarse_solve(prob.ptr, _dptr(f, nn, "f"), _dptr(z, nn, "z"), _stream(stream)),
            "dcg_coarse_solve")
 
 
@@ -351,8 +362,23 @@ def dcg_profile_read(prob: Problem, stream=None) -> dict:
 
 def dcg_coarse_solve_static(prob: Problem, f, z, stream=None):
     """Allocation-free coarsest solve (fixed device scratch inside the library)."""
-    _check(load().dcg_coarse_solve_static(prob.ptr, _dptr(f, name="f"), _dptr(z, name="z"), _stream(stream)),
+    nn = prob.level_nodes(1)
+    _check(load().dcg_coarse_solve_static(prob.ptr, _dptr(f, nn, "f"), _dptr(z, nn, "z"), _stream(stream)),
            "dcg_coarse_solve_static")
+
+
+def dcg_measure_fma_rate(precision, stream=None) -> float:
+    """Measured FMA rate (TFLOP/s) of the FP64 (DCG_FP64) or FP32 (DCG_MIXED) pipes."""
+    t = C.c_double()
+    _check(load().dcg_measure_fma_rate(precision, C.byref(t), _stream(stream)), "dcg_measure_fma_rate")
+    return t.value
+
+
+def dcg_selftest_bounded_wait(max_polls, stream=None) -> bool:
+    """True when the bounded mbarrier wait gave up after max_polls polls."""
+    g = C.c_int()
+    _check(load().dcg_selftest_bounded_wait(max_polls, C.byref(g), _stream(stream)), "dcg_selftest_bounded_wait")
+    return bool(g.value)
 
 
 def dcg_kernel_launches() -> int:

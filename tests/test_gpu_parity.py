@@ -6,7 +6,9 @@ embed/extract and stencil products to 1e-12; FP64 smoother, coarse solve and
 W-cycles to 1e-10; solves at true relative residual 1e-8 to 1e-7 relative
 error with outer iteration counts within +-2. Mixed precision (FP32
 W-cycle) is held to its own bars (FP32 rounding, ~1e-5) and the same
-true-residual target.
+true-residual target. Kernel-level comparisons are element by element:
+max |gpu - oracle| over max |oracle| (a wrong boundary row or tile seam
+cannot hide behind a norm).
 """
 import numpy as np
 import pytest
@@ -44,11 +46,19 @@ def relerr(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def maxrel(a, b):
+    """Element-wise error: max |a - b| / max |b|."""
+    a, b = np.asarray(a), np.asarray(b)
+    assert a.shape == b.shape
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
 def mg_opts(patch=4, overlap=1, m1=2, m2=2, max_levels=4, weights="multiplicity"):
     return mg.MGOptions(patch=patch, overlap=overlap, m1=m1, m2=m2, max_levels=max_levels, ras_weights=weights)
 
 
 def gpu_opts(o: mg.MGOptions, **kw):
+    kw.setdefault("stall_window", 0)  # the oracle's default: Algorithm 2 without the stall rule
     return dcg.options(patch=o.patch, overlap=o.overlap, m1=o.m1, m2=o.m2, max_levels=o.max_levels,
                        ras_weights=dcg.DCG_RAS_RESTRICTED if o.ras_weights == "restricted" else dcg.DCG_RAS_MULTIPLICITY,
                        **kw)
@@ -90,7 +100,7 @@ def test_spmv(d, n, dt):
     x = inputs.rhs(7, asm.mesh.n_unknowns)
     y = torch.empty(prob.N, dtype=torch.float64, device="cuda")
     dcg.dcg_spmv(prob, dev(x), y)
-    assert relerr(host(y), asm.matrix() @ x) <= 1e-12
+    assert maxrel(host(y), asm.matrix() @ x) <= 1e-12
 
 
 @pytest.mark.parametrize("d,n", [(2, 1024), (3, 128)])
@@ -108,7 +118,7 @@ def test_spmv_full_size_sampled_rows(d, n):
     nodes = np.unique(np.concatenate([[0, 1, mesh.m - 1, mesh.m, mesh.n_nodes // 2, mesh.n_nodes - 1],
                                       rng.integers(0, mesh.n_nodes, 40)]))
     want = fem.rows_of_Ax(mesh, dt, x, nodes)
-    assert relerr(yh[nodes], want) <= 1e-12
+    assert maxrel(yh[nodes], want) <= 1e-12
     prob.close()
 
 
@@ -119,7 +129,7 @@ def test_embed_extract(d, n):
     y = inputs.rhs(3, mesh.n_unknowns)
     q = torch.empty(prob.n_nodes, dtype=torch.float64, device="cuda")
     dcg.dcg_extract(prob, dev(y), q)
-    assert relerr(host(q), fem.extract(mesh, y)) <= 1e-15
+    assert maxrel(host(q), fem.extract(mesh, y)) <= 1e-15
     qq = inputs.rhs(4, mesh.n_nodes)
     yy = torch.empty(prob.N, dtype=torch.float64, device="cuda")
     dcg.dcg_embed(prob, dev(qq), yy)
@@ -146,7 +156,7 @@ def test_inner_operator(d, n, dt):
     z = inputs.rhs(9, asm.mesh.n_nodes)
     y = torch.empty_like(dev(z))
     dcg.dcg_inner_apply(prob, dev(z), y)
-    assert relerr(host(y), H.levels[-1].Z @ z) <= 1e-12
+    assert maxrel(host(y), H.levels[-1].Z @ z) <= 1e-12
 
 
 @pytest.mark.parametrize("d,n,P,o", [(2, 32, 4, 1), (2, 20, 4, 1), (2, 32, 8, 2), (3, 8, 4, 1), (3, 12, 4, 1),
@@ -160,7 +170,7 @@ def test_ras_step(d, n, P, o, weights):
         z = inputs.rhs(40 + k, nn)
         zt = dev(z)
         dcg.dcg_ras_step(prob, k, dev(f), zt)
-        assert relerr(host(zt), H.ras_step(k, f, z)) <= 1e-11, k
+        assert maxrel(host(zt), H.ras_step(k, f, z)) <= 1e-11, k
 
 
 @pytest.mark.parametrize("d,n", [(2, 32), (2, 64), (3, 8), (3, 16), (2, 2), (2, 3)])
@@ -170,7 +180,7 @@ def test_coarse_solve(d, n):
     f = inputs.rhs(5, nn)
     z = torch.empty_like(dev(f))
     dcg.dcg_coarse_solve(prob, dev(f), z)
-    assert relerr(host(z), H.coarse_solve(f)) <= 1e-11
+    assert maxrel(host(z), H.coarse_solve(f)) <= 1e-11
 
 
 @pytest.mark.parametrize("d,n,P,o", [(2, 32, 4, 1), (2, 40, 4, 1), (3, 8, 4, 1), (3, 16, 4, 1), (2, 64, 8, 2)])
@@ -183,7 +193,7 @@ def test_wcycles(d, n, P, o):
         z = np.zeros_like(g)
         for _ in range(ncyc):
             z = H.wcycle(g, z)
-        assert relerr(host(zt), z) <= 1e-10, ncyc
+        assert maxrel(host(zt), z) <= 1e-10, ncyc
 
 
 @pytest.mark.parametrize("d,n", [(2, 32), (3, 8)])
@@ -193,12 +203,12 @@ def test_wcycles_mixed(d, n):
     zt = torch.zeros(prob.n_nodes, dtype=torch.float64, device="cuda")
     dcg.dcg_mg_cycles(prob, dev(g), zt, 1)
     z = H.wcycle(g, np.zeros_like(g))
-    assert relerr(host(zt), z) <= 1e-5
+    assert maxrel(host(zt), z) <= 1e-5
     # FP64 residuals make the FP32 cycle converge to FP64 accuracy
     zt.zero_()
     ncyc = dcg.dcg_mg_solve(prob, dev(g), zt, 1e-11)
     zo, no = H.multigrid(g, 1e-11, 100)
-    assert relerr(host(zt), zo) <= 1e-9
+    assert maxrel(host(zt), zo) <= 1e-9
     assert abs(ncyc - no) <= 2
 
 
@@ -211,27 +221,30 @@ def test_mg_solve_counts(d, n):
         ncyc = dcg.dcg_mg_solve(prob, dev(g), zt, tol)
         zo, no = H.multigrid(g, tol, 100)
         assert ncyc == no
-        assert relerr(host(zt), zo) <= 1e-9
+        assert maxrel(host(zt), zo) <= 1e-9
 
 
 # --------------------------------------------------------------------------- solves
 
 
+RULES = {"fixed": dcg.DCG_INNER_FIXED, "adaptive": dcg.DCG_INNER_ADAPTIVE, "exact": dcg.DCG_INNER_EXACT}
+RECS = {"fcg1": dcg.DCG_FCG1, "fr": dcg.DCG_FR, "fcg_inf": dcg.DCG_FCG_INF}
+
+
 def _solve_pair(d, n, dt, o: mg.MGOptions, rule="fixed", rec="fcg1", c=0.01, precision=dcg.DCG_FP64, seed=0,
-                deflate=True):
+                deflate=True, m_max=None, ras_inverse=dcg.DCG_INV_FP32, max_it=100000):
     asm = fem.assemble(d, n, dt)
     f = inputs.rhs(seed, asm.mesh.n_unknowns)
     prob = dcg.dcg_assemble(d, n, dt)
-    rules = {"fixed": dcg.DCG_INNER_FIXED, "adaptive": dcg.DCG_INNER_ADAPTIVE, "exact": dcg.DCG_INNER_EXACT}
-    recs = {"fcg1": dcg.DCG_FCG1, "fr": dcg.DCG_FR, "fcg_inf": dcg.DCG_FCG_INF}
-    dcg.dcg_setup(prob, gpu_opts(o, inner_rule=rules[rule], recurrence=recs[rec], c=c, precision=precision,
-                                 deflate=int(deflate)))
+    dcg.dcg_setup(prob, gpu_opts(o, inner_rule=RULES[rule], recurrence=RECS[rec], c=c, precision=precision,
+                                 deflate=int(deflate), fcg_max_dirs=m_max or 0, ras_inverse=ras_inverse))
     x = torch.zeros(prob.N, dtype=torch.float64, device="cuda")
-    st = dcg.dcg_solve(prob, dev(f), x, tol=1e-8)
+    st = dcg.dcg_solve(prob, dev(f), x, tol=1e-8, max_it=max_it)
     if deflate:
-        x_o, st_o = solvers.FDCG(asm, solvers.FDCGOptions(mg=o, inner_rule=rule, recurrence=rec, c=c)).solve(f)
+        x_o, st_o = solvers.FDCG(asm, solvers.FDCGOptions(mg=o, inner_rule=rule, recurrence=rec, c=c,
+                                                          m_max=m_max)).solve(f, max_it=max_it)
     else:
-        x_o, st_o = solvers.plain_cg(asm.matrix(), f)
+        x_o, st_o = solvers.plain_cg(asm.matrix(), f, max_it=max_it)
     return host(x), st, x_o, st_o, asm, f
 
 
@@ -249,6 +262,7 @@ def test_plain_cg(d, n, dt):
 def test_dcg_fp64(d, n, dt, rule):
     x, st, x_o, st_o, asm, f = _solve_pair(d, n, dt, mg_opts(), rule=rule)
     assert st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8, st
+    assert st["restarts"] == 0 and st_o.restarts == 0
     assert abs(st["outer_its"] - st_o.outer_its) <= 2, (st, st_o.outer_its)
     if rule != "exact":
         assert abs(st["total_mg_cycles"] - st_o.total_mg_cycles) <= max(4, 0.05 * st_o.total_mg_cycles)
@@ -261,8 +275,10 @@ def test_dcg_fp64(d, n, dt, rule):
 def test_dcg_recurrences(rec):
     x, st, x_o, st_o, asm, f = _solve_pair(2, 32, 1e-4, mg_opts(), rec=rec)
     assert st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8
+    assert st["restarts"] == 0 and st_o.restarts == 0
     assert abs(st["outer_its"] - st_o.outer_its) <= 2
     assert relerr(x, x_o) <= 1e-7
+    assert st["fcg_truncated"] == 0
 
 
 @pytest.mark.parametrize("window", [0, 50])
@@ -284,7 +300,8 @@ def test_dcg_stall_restart(window):
     else:
         assert st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8 and st["restarts"] >= 1
         assert st_o.converged
-        assert abs(st["outer_its"] - st_o.outer_its) <= max(2, 0.25 * st_o.outer_its)
+        assert st["restarts"] == st_o.restarts
+        assert abs(st["outer_its"] - st_o.outer_its) <= 2
         assert relerr(host(x), x_o) <= 1e-7
 
 
@@ -292,6 +309,7 @@ def test_dcg_stall_restart(window):
 def test_dcg_mixed(d, n, dt):
     x, st, x_o, st_o, asm, f = _solve_pair(d, n, dt, mg_opts(), precision=dcg.DCG_MIXED)
     assert st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8
+    assert st["restarts"] == 0
     assert abs(st["outer_its"] - st_o.outer_its) <= 3
     assert relerr(x, x_o) <= 1e-7
 

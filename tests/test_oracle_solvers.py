@@ -172,3 +172,96 @@ def test_stall_restart_recovers_from_stagnation():
     x, st = solvers.FDCG(asm, solvers.FDCGOptions(mg=o, c=50.0, stall_window=50)).solve(f, max_it=1500)
     assert st.converged and st.true_relres <= 1e-8 and st.restarts >= 1 and st.outer_its < 500
     assert np.linalg.norm(f - asm.matrix() @ x) <= 1e-8 * np.linalg.norm(f)
+
+
+def test_adaptive_inner_tolerance_follows_eq_tol():
+    """Eq. tol: at outer iteration i the multigrid inside M_D gets
+    tau_c = c_A * tol * ||f|| / ||r_i||, r_i the current recursive deflated
+    residual (r_0 = f_D for the first iteration). The norms come from the
+    residual history the outer loop records; a slip such as c * tol,
+    c * eps * ||r_i|| or the previous residual fails here."""
+    asm = fem.assemble(2, 16, 1e-5)
+    f = _f(asm, seed=2)
+    tol, c = 1e-8, 0.02
+    x, st = solvers.FDCG(asm, solvers.FDCGOptions(inner_rule="adaptive", c=c)).solve(f, tol=tol)
+    assert st.converged and st.restarts == 0
+    r = [st.res0[0]] + list(st.history)
+    assert len(st.inner_tols) == st.outer_its
+    fn = np.linalg.norm(f)
+    for i, tc in enumerate(st.inner_tols):
+        assert np.isclose(tc, c * tol * fn / r[i], rtol=1e-12, atol=0.0), i
+    # the tolerance loosens as the outer residual falls, and is at most c_A
+    # when the outer iteration stops (||r|| ~ tol ||f||)
+    assert st.inner_tols[-1] > 100 * st.inner_tols[0]
+    assert st.inner_tols[-1] <= 10 * c
+
+
+def test_fixed_inner_tolerance_is_c_times_tol():
+    """Eq. fixed_tol with the experiments' reading: tau_c = c_F * tol at every
+    outer iteration."""
+    asm = fem.assemble(2, 16, 1e-5)
+    f = _f(asm, seed=2)
+    x, st = solvers.FDCG(asm, solvers.FDCGOptions(inner_rule="fixed", c=0.01)).solve(f, tol=1e-8)
+    assert st.inner_tols and all(t == 0.01 * 1e-8 for t in st.inner_tols)
+
+
+def test_adaptive_tolerance_cuts_total_cycles():
+    """Table 3 trend: the adaptive rule needs far fewer W-cycles in total
+    (Tot) than the fixed rule with the same constant, at the same outer count."""
+    for dt in [1e-4, 1e-6]:
+        asm = fem.assemble(2, 32, dt)
+        f = _f(asm)
+        _, st_f = solvers.FDCG(asm, solvers.FDCGOptions(inner_rule="fixed", c=0.01)).solve(f)
+        _, st_a = solvers.FDCG(asm, solvers.FDCGOptions(inner_rule="adaptive", c=0.01)).solve(f)
+        assert st_f.converged and st_a.converged
+        assert abs(st_f.outer_its - st_a.outer_its) <= 2
+        assert st_a.total_mg_cycles < 0.8 * st_f.total_mg_cycles, (dt, st_a.total_mg_cycles, st_f.total_mg_cycles)
+        assert st_a.avg_inner < st_f.avg_inner - 1.0
+
+
+def test_truncated_fcg_special_cases():
+    """Remark after Table 4: m_i = max{1, mod(i, m_max + 1)}. m_max = 0 is
+    FCG(1) and an m_max beyond the iteration count is the untruncated
+    FCG(inf), both bit for bit; with exact inner solves every truncation gives
+    the iterates of classical CG (the directions are conjugate already)."""
+    asm = fem.assemble(2, 16, 1e-4)
+    f = _f(asm, seed=1)
+    o = mg.MGOptions(patch=4, overlap=1, max_levels=2)
+
+    def run(rec, m_max=None, rule="adaptive"):
+        return solvers.FDCG(asm, solvers.FDCGOptions(mg=o, inner_rule=rule, c=0.05, recurrence=rec,
+                                                     m_max=m_max)).solve(f)
+
+    x1, s1 = run("fcg1")
+    x0, s0 = run("fcg_inf", 0)
+    assert s0.history == s1.history and np.array_equal(x0, x1)
+    xi, si = run("fcg_inf")
+    xb, sb = run("fcg_inf", 10 * si.outer_its)
+    assert sb.history == si.history and np.array_equal(xb, xi)
+    # a truncation that actually restarts differs from both ends
+    x3, s3 = run("fcg_inf", 3)
+    assert s3.converged and s3.history != s1.history and s3.history != si.history
+    he = {}
+    for m_max in [None, 2, 5]:
+        _, st = solvers.FDCG(asm, solvers.FDCGOptions(inner_rule="exact", recurrence="fcg_inf",
+                                                      m_max=m_max)).solve(f, tol=1e-10)
+        he[m_max] = np.array(st.history[:15])
+    _, st_fr = solvers.FDCG(asm, solvers.FDCGOptions(inner_rule="exact", recurrence="fr")).solve(f, tol=1e-10)
+    for m_max, h in he.items():
+        assert np.allclose(h, np.array(st_fr.history[:15]), rtol=1e-7), m_max
+
+
+def test_fcg1_breaks_down_where_fcg_inf_does_not():
+    """Tables 3-4 trend on Q1: with a loose adaptive inner tolerance the
+    inexact deflated operator stops being positive on the FCG(1) direction
+    ((d, M_D d) <= 0: the paper's failed runs), while FCG(inf), which keeps
+    every direction, goes on reducing the residual."""
+    asm = fem.assemble(2, 12, 0.1)
+    f = inputs.rhs(5, asm.mesh.n_unknowns)
+    o = mg.MGOptions(patch=4, overlap=1, max_levels=2)
+    opts = dict(mg=o, inner_rule="adaptive", c=0.2, max_restarts=0)
+    _, s1 = solvers.FDCG(asm, solvers.FDCGOptions(recurrence="fcg1", **opts)).solve(f, max_it=400)
+    _, si = solvers.FDCG(asm, solvers.FDCGOptions(recurrence="fcg_inf", **opts)).solve(f, max_it=400)
+    assert s1.breakdown and not s1.converged and s1.outer_its < 400
+    assert not si.breakdown and si.outer_its == 400
+    assert si.true_relres < 0.1 * s1.true_relres

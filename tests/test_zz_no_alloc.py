@@ -32,11 +32,14 @@ def _coarse_nodes(d, n, levels):
     return (mg.level_sizes(n, levels)[-1] - 1) ** d
 
 
-@pytest.mark.parametrize("d,n,levels", [(2, 64, 4), (2, 256, 2), (3, 32, 2)])
+# m + 1 a power of two (sine transforms by FFT: 8, 128, 16) and not (dense
+# passes with the sine matrix: 48, 12), so both routes use the static scratch
+@pytest.mark.parametrize("d,n,levels", [(2, 64, 4), (2, 256, 2), (3, 32, 2), (2, 96, 2), (3, 24, 2)])
 def test_static_matches_allocating_twice(d, n, levels):
     prob = dcg.dcg_assemble(d, n, 1e-3)
     dcg.dcg_setup(prob, dcg.options(max_levels=levels))  # FP64 cycle
     nn = _coarse_nodes(d, n, levels)
+    assert prob.level_nodes(1) == nn
     for call in range(2):  # the shared scratch keeps the previous call's contents
         f = torch.from_numpy(inputs.rhs(30 + call, nn)).cuda()
         z_ref = torch.empty_like(f)
