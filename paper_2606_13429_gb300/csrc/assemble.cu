@@ -214,7 +214,10 @@ int assemble_device(dcg_problem* p, const double* nu_elem_host, cudaStream_t s) 
   }
   if (p->matrix_free) return DCG_OK;
   DCG_CUDA(cudaMalloc(&p->row_ptr, sizeof(int) * (nn + 1)));
-  DCG_CUDA(cudaMalloc(&p->col_idx, sizeof(int) * p->nnzb));
+  // four spare entries: bulk copies of a column range start and end on
+  // 16-byte boundaries and may read up to three entries past the last one
+  DCG_CUDA(cudaMalloc(&p->col_idx, sizeof(int) * (p->nnzb + 4)));
+  DCG_CUDA(cudaMemsetAsync(p->col_idx + p->nnzb, 0, sizeof(int) * 4, s));
   DCG_CUDA(cudaMalloc(&p->vals, sizeof(double) * p->nnzb * p->b * p->b));
   int g = (int)((nn + threads - 1) / threads);
   if (D == 2) k_pattern<2><<<g, threads, 0, s>>>(p->m, nn, p->row_ptr, p->col_idx);

@@ -152,6 +152,8 @@ struct RasClass {
   int local_off;      // offset of the class's packed local coordinates
   int nb;             // boxes per work item (batch width of the product)
   long long inv_off;  // offset of the inverse in the level's inverse array
+  int fdm_s[kMaxDim]; // fast diagonalisation: offset of each axis's sine matrix in the level's table
+  long long fdm_tri;  // fast diagonalisation: offset of the line-solve factors along the last axis
 };
 
 struct Level {
@@ -180,6 +182,10 @@ struct Level {
   long long ras_np2 = 0;            // sum over boxes of np^2 (FMAs of one smoothing product)
   long long gmax = 0;               // max over classes of np * nb (residual tile elements)
   bool tc = false;                  // RAS products on the tensor cores (BF16 inverses)
+  bool fdm = false;                 // FP64 local solves by fast diagonalisation and line solves
+  int fdm_lmax = 0;                 // largest box extent along an axis (register bound of the kernel)
+  double* d_fdm = nullptr;          // sine matrices and line-solve factors of every class
+  double fdm_flops = 0.0;           // algorithmic flops of one fast-diagonalisation smoothing product
   void* d_inv = nullptr;            // inverses in the W-cycle precision (row-major, symmetric)
   void* d_inv_bf16 = nullptr;       // optional BF16 copy
   // vectors in the W-cycle precision
@@ -309,6 +315,8 @@ void prof_clear_graph(dcg_problem* p);
 
 // launchers implemented in the .cu files
 int assemble_device(dcg_problem* p, const double* nu_elem_host, cudaStream_t s);
+// per-device kernel attributes of the BSR products (called by dcg_assemble)
+int spmv_init(dcg_problem* p);
 int spmv_plain(dcg_problem* p, const double* x, double* y, cudaStream_t s, bool lowp = false);
 // y = A x with dot(dv, y) into scal[slot] when dv != nullptr
 int spmv_dot(dcg_problem* p, const double* x, double* y, const double* dv, int slot, cudaStream_t s);

@@ -627,6 +627,149 @@ __global__ void __launch_bounds__(256) k_ras_solve_tc(RasArgs ra, const float* _
   if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
+
+// (1'') FP64 local solves by fast diagonalisation. On a level whose stencil
+// is the Q1 Laplacian / d (checked at setup), a box's local matrix
+// R_i Z_k R_i^T is (1/d) sum_i (x)_ax {K_l if ax = i else M_l} with the 1D
+// Dirichlet matrices K_l = (1/h) tridiag(-1, 2, -1) and M_l = (h/6)
+// tridiag(1, 4, 1) of the box extents l, both diagonalised by the orthonormal
+// sine matrix S_l. The exact solve (A_k)_i^{-1} g is then: S along every axis
+// but the last, one tridiagonal solve per line along the last axis (the
+// operator restricted to each transformed line is tridiagonal, symmetric and
+// diagonally dominant; its elimination factors are precomputed), S back.
+// Per 12 x 12 box that is about 3,900 FP64 operations instead of the 20,736
+// of the dense inverse: this GPU issues FP64 at a small fraction of its FP32
+// rate, so the count of FP64 operations is what the FP64 smoother costs.
+// A CTA takes one work item (boxes of one class); every phase gives each
+// thread one grid line of one box (box index fastest), the box values live
+// in shared memory with an odd row stride (np + 1), lines in registers (LM
+// = the largest extent, a compile-time bound). Results are written in the
+// work item's layout y[item][i][nb] that k_ras_update reads.
+// S applied along one grid line of length l (entries base + x * stride),
+// in place. Row j of the sine matrix is symmetric (j even) or antisymmetric
+// (j odd) about the line's midpoint, so the line is folded once into
+// p_x = v_x + v_{l-1-x} and q_x = v_x - v_{l-1-x} (x < l/2) and each output
+// takes l/2 FMAs (plus the middle entry for odd l and even j): about
+// l + l^2/2 FP64 operations instead of l^2.
+template <int LM>
+__device__ __forceinline__ void fdm_line_transform(double* __restrict__ W, int base, int stride, int l,
+                                                   const double* __restrict__ S, double* __restrict__ out = nullptr,
+                                                   long long out_stride = 0) {
+  constexpr int HM = (LM + 1) / 2;
+  const int h = l >> 1;
+  double pe[HM], qo[HM];
+#pragma unroll
+  for (int x = 0; x < HM; ++x) {
+    if (x < h) {
+      const double a = W[base + x * stride], b = W[base + (l - 1 - x) * stride];
+      pe[x] = a + b;
+      qo[x] = a - b;
+    } else {
+      pe[x] = 0.0;
+      qo[x] = 0.0;
+    }
+  }
+  const double mid = (l & 1) ? W[base + h * stride] : 0.0;
+#pragma unroll
+  for (int j = 0; j < LM; ++j) {
+    if (j < l) {
+      const double* Sj = S + j * l;
+      double acc = 0.0;
+      if (j & 1) {
+#pragma unroll
+        for (int x = 0; x < HM; ++x)
+          if (x < h) acc = fma(__ldg(Sj + x), qo[x], acc);
+      } else {
+        if (l & 1) acc = __ldg(Sj + h) * mid;
+#pragma unroll
+        for (int x = 0; x < HM; ++x)
+          if (x < h) acc = fma(__ldg(Sj + x), pe[x], acc);
+      }
+      if (out) out[j * out_stride] = acc;
+      else W[base + j * stride] = acc;
+    }
+  }
+}
+
+template <int LM>
+__device__ __forceinline__ void fdm_line_solve(double* __restrict__ W, int base, int stride, int n,
+                                               const double* __restrict__ t) {
+  // t = [b, l_0, winv_0, l_1, winv_1, ...]: y_i = g_i - l_i y_{i-1};
+  // x_{n-1} = y_{n-1} winv_{n-1}; x_i = (y_i - b x_{i+1}) winv_i
+  double g[LM];
+#pragma unroll
+  for (int i = 0; i < LM; ++i) g[i] = i < n ? W[base + i * stride] : 0.0;
+#pragma unroll
+  for (int i = 1; i < LM; ++i)
+    if (i < n) g[i] = fma(-__ldg(t + 1 + 2 * i), g[i - 1], g[i]);
+  const double b = __ldg(t);
+  double xn = 0.0;
+#pragma unroll
+  for (int i = LM - 1; i >= 0; --i) {
+    if (i < n) {
+      const double xi = fma(-b, xn, g[i]) * __ldg(t + 2 + 2 * i);  // xn = 0 for i = n - 1: exactly g[i]
+      W[base + i * stride] = xi;
+      xn = xi;
+    }
+  }
+}
+
+template <int D, int LM>
+__global__ void __launch_bounds__(128) k_ras_fdm(RasArgs ra, const double* __restrict__ rvec,
+                                                 const double* __restrict__ tab, double* __restrict__ y) {
+  extern __shared__ __align__(16) double W[];
+  const int w = blockIdx.x;
+  const int cls = ra.work[3 * w], first = ra.work[3 * w + 1], cnt = ra.work[3 * w + 2];
+  const RasClass C = ra.classes[cls];
+  const int lx = C.len[0], ly = C.len[1], lz = D > 2 ? C.len[2] : 1;
+  const int np = C.np, ld = np + 1, NB = C.nb;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // gather the residual on the boxes
+  for (int t = tid; t < cnt * np; t += nt) {
+    const int b = t / np, i = t - b * np;
+    const int node0 = __ldg(ra.origin + __ldg(ra.class_patches + first + b)).w;
+    W[b * ld + i] = __ldg(rvec + node0 + __ldg(ra.local_off_node + C.local_off + i));
+  }
+  __syncthreads();
+  const double* Sx = tab + C.fdm_s[0];
+  const double* Sy = tab + C.fdm_s[1];
+  // forward transforms along x (and y in 3D)
+  for (int t = tid; t < cnt * ly * lz; t += nt) {
+    const int b = t % cnt, line = t / cnt;
+    fdm_line_transform<LM>(W, b * ld + line * lx, 1, lx, Sx);
+  }
+  __syncthreads();
+  if (D > 2) {
+    for (int t = tid; t < cnt * lx * lz; t += nt) {
+      const int b = t % cnt, line = t / cnt, j = line % lx, z = line / lx;
+      fdm_line_transform<LM>(W, b * ld + j + z * lx * ly, lx, ly, Sy);
+    }
+    __syncthreads();
+  }
+  // tridiagonal solves along the last axis, one per transformed line
+  {
+    const int nlines = D > 2 ? lx * ly : lx, n = D > 2 ? lz : ly, stride = D > 2 ? lx * ly : lx;
+    for (int t = tid; t < cnt * nlines; t += nt) {
+      const int b = t % cnt, line = t / cnt;
+      fdm_line_solve<LM>(W, b * ld + line, stride, n, tab + C.fdm_tri + (long long)line * (1 + 2 * n));
+    }
+  }
+  __syncthreads();
+  if (D > 2) {
+    for (int t = tid; t < cnt * lx * lz; t += nt) {
+      const int b = t % cnt, line = t / cnt, j = line % lx, z = line / lx;
+      fdm_line_transform<LM>(W, b * ld + j + z * lx * ly, lx, ly, Sy);
+    }
+    __syncthreads();
+  }
+  // back along x, results to the work item's layout (box index fastest)
+  double* yi = y + ra.item_off[w];
+  for (int t = tid; t < cnt * ly * lz; t += nt) {
+    const int b = t % cnt, line = t / cnt;
+    fdm_line_transform<LM>(W, b * ld + line * lx, 1, lx, Sx, yi + (size_t)line * lx * NB + b, NB);
+  }
+}
+
 // symmetrised inverse as BF16 in the canonical K-major layout, padded to npad
 __global__ void k_inv_bf16_canon(const double* __restrict__ a, __nv_bfloat16* __restrict__ out, int n, int npad) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -666,7 +809,9 @@ __global__ void k_ras_update(const int* __restrict__ ysrc, const T* __restrict__
           ++mult;
         }
     }
-    z[a] += restricted ? s : s / (T)mult;
+    // multiplicities are products of 1s and 2s (a node lies in at most two
+    // boxes per axis): their reciprocals are exact, so this equals s / mult
+    z[a] += restricted ? s : s * ((T)1 / (T)mult);
   }
 }
 
@@ -1145,7 +1290,7 @@ void free_level(Level& L) {
   cudaFree(L.d_patch_class); cudaFree(L.d_work); cudaFree(L.d_class_patches);
   cudaFree(L.d_classes); cudaFree(L.d_origin); cudaFree(L.d_core); cudaFree(L.d_local); cudaFree(L.d_axis_tab);
   cudaFree(L.d_local_node); cudaFree(L.d_item_off); cudaFree(L.d_ysrc); cudaFree(L.r);
-  cudaFree(L.d_inv); cudaFree(L.d_inv_bf16); cudaFree(L.f); cudaFree(L.z); cudaFree(L.y);
+  cudaFree(L.d_inv); cudaFree(L.d_inv_bf16); cudaFree(L.f); cudaFree(L.z); cudaFree(L.y); cudaFree(L.d_fdm);
   L = Level{};
 }
 
@@ -1308,12 +1453,97 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
   DCG_CUDA(cudaMemcpyAsync(L.d_class_patches, grouped.data(), sizeof(int) * grouped.size(), cudaMemcpyHostToDevice, s));
   DCG_CUDA(cudaMemcpyAsync(L.d_work, work.data(), sizeof(int) * work.size(), cudaMemcpyHostToDevice, s));
   DCG_CUDA(cudaMemcpyAsync(L.d_classes, L.classes.data(), sizeof(RasClass) * L.nclass, cudaMemcpyHostToDevice, s));
-  // local inverses: box matrix from the stencil, Gauss-Jordan in FP64
   const size_t tsz = fp32 ? sizeof(float) : sizeof(double);
+  // FP64 levels whose stencil is the Q1 Laplacian / d: local solves by fast
+  // diagonalisation (sine matrices per box extent, elimination factors of the
+  // line solves along the last axis), computed here in FP64
+  L.fdm = false;
+  if (!fp32) {
+    int lmax = 0;
+    for (const auto& c : L.classes)
+      for (int k = 0; k < D; ++k) lmax = std::max(lmax, c.len[k]);
+    const double h = 1.0 / L.n;
+    const Stencil<double> cf = q1_laplacian_over_d(D, h);
+    double dev = 0.0, mx = 0.0;
+    for (int k = 0; k < 27; ++k) {
+      dev = std::max(dev, std::fabs(cf.c[k] - L.st64.c[k]));
+      mx = std::max(mx, std::fabs(cf.c[k]));
+    }
+    if (dev <= 1e-12 * mx && lmax <= (D == 2 ? 16 : 6)) {
+      std::vector<double> tab;
+      std::map<int, int> s_off;  // extent -> offset of its sine matrix
+      auto sine = [&](int l) {
+        auto it = s_off.find(l);
+        if (it != s_off.end()) return it->second;
+        const int off = (int)tab.size();
+        for (int j = 0; j < l; ++j)
+          for (int x = 0; x < l; ++x)
+            tab.push_back(std::sqrt(2.0 / (l + 1)) * std::sin(M_PI * (double)((j + 1) * (x + 1)) / (l + 1)));
+        s_off[l] = off;
+        return off;
+      };
+      auto kap = [&](int l, int j) { return (2.0 / h) * (1.0 - std::cos(M_PI * (j + 1) / (l + 1))); };
+      auto mu = [&](int l, int j) { return (h / 3.0) * (2.0 + std::cos(M_PI * (j + 1) / (l + 1))); };
+      for (auto& c : L.classes) {
+        for (int k = 0; k < D; ++k) c.fdm_s[k] = sine(c.len[k]);
+        c.fdm_tri = (long long)tab.size();
+        const int n = c.len[D - 1];
+        const int nsys = D == 2 ? c.len[0] : c.len[0] * c.len[1];
+        for (int sys = 0; sys < nsys; ++sys) {
+          // operator along the last axis after the transforms: a M_n + b K_n
+          // (2D: (kap_j M + mu_j K) / 2; 3D: ((kap_j mu_k + mu_j kap_k) M + mu_j mu_k K) / 3)
+          double cm, ck;
+          if (D == 2) {
+            cm = kap(c.len[0], sys) / 2.0;
+            ck = mu(c.len[0], sys) / 2.0;
+          } else {
+            const int j = sys % c.len[0], k = sys / c.len[0];
+            cm = (kap(c.len[0], j) * mu(c.len[1], k) + mu(c.len[0], j) * kap(c.len[1], k)) / 3.0;
+            ck = mu(c.len[0], j) * mu(c.len[1], k) / 3.0;
+          }
+          const double a = cm * (4.0 * h / 6.0) + ck * (2.0 / h);
+          const double b = cm * (h / 6.0) - ck * (1.0 / h);
+          tab.push_back(b);
+          double wprev = 0.0;
+          for (int i = 0; i < n; ++i) {
+            const double li = i == 0 ? 0.0 : b / wprev;
+            const double wi = a - li * b;
+            tab.push_back(li);
+            tab.push_back(1.0 / wi);
+            wprev = wi;
+          }
+        }
+      }
+      DCG_CUDA(cudaMalloc(&L.d_fdm, sizeof(double) * tab.size()));
+      DCG_CUDA(cudaMemcpyAsync(L.d_fdm, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s));
+      DCG_CUDA(cudaMemcpyAsync(L.d_classes, L.classes.data(), sizeof(RasClass) * L.nclass, cudaMemcpyHostToDevice, s));
+      DCG_CUDA(cudaStreamSynchronize(s));  // the host table goes out of scope
+      L.fdm = true;
+      L.fdm_lmax = lmax;
+      // algorithmic flops of one smoothing product (an FMA counts 2): folded
+      // transforms along every axis but the last, forward and back, and the
+      // line solves along the last
+      L.fdm_flops = 0.0;
+      for (int pid = 0; pid < L.npatch; ++pid) {
+        const RasClass& c = L.classes[pclass[pid]];
+        const int n = c.len[D - 1];
+        double per = (double)(c.np / n) * (5.0 * n - 2.0);  // line solves
+        for (int k = 0; k < D - 1; ++k) {
+          const int l = c.len[k], h = l / 2;
+          per += 2.0 * (double)(c.np / l) * (2.0 * h + 2.0 * l * h);  // folded transforms, forward and back
+        }
+        L.fdm_flops += per;
+      }
+    }
+  }
+  // local inverses: box matrix from the stencil, Gauss-Jordan in FP64 (not
+  // needed when the level solves its boxes by fast diagonalisation)
+  if (L.fdm) inv_total = 1;
   DCG_CUDA(cudaMalloc(&L.d_inv, (L.tc ? sizeof(__nv_bfloat16) : tsz) * inv_total));
   double* work64 = nullptr;
   DCG_CUDA(cudaMalloc(&work64, sizeof(double) * (size_t)L.npmax * L.npmax));
   for (auto& c : L.classes) {
+    if (L.fdm) break;
     const int np = c.np;
     const long long nel = (long long)np * np;
     const int g = (int)((nel + 255) / 256);
@@ -1384,6 +1614,13 @@ int coarse_solve_t(dcg_problem* p, const T* f, T* z, cudaStream_t s) {
   return DCG_OK;
 }
 
+// shared memory of k_ras_fdm: the boxes of one work item, rows of np + 1
+size_t fdm_smem_bytes(const Level& L) {
+  size_t mx = 0;
+  for (const auto& c : L.classes) mx = std::max(mx, sizeof(double) * (size_t)c.nb * (c.np + 1));
+  return mx;
+}
+
 template <typename T, int D>
 int ras_step_t(dcg_problem* p, Level& L, cudaStream_t s, bool z_zero = false) {
   RasArgs ra{};
@@ -1431,6 +1668,32 @@ int ras_step_t(dcg_problem* p, Level& L, cudaStream_t s, bool z_zero = false) {
                                                       (float*)L.y);
       DCG_LAUNCH_CHECK();
       prof_end(p, prof, s, flops, bytes, g_capturing);
+      prof = prof_begin(p, PC_RAS_UPDATE, s, g_capturing);
+      k_ras_update<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(L.d_ysrc, (const T*)L.y, (T*)L.z, L.nn,
+                                                                    p->opts.ras_weights == DCG_RAS_RESTRICTED);
+      DCG_LAUNCH_CHECK();
+      prof_end(p, prof, s, (double)L.nn * (1 << D),
+               (double)L.nn * ((1 << D) * (4.0 + sizeof(T)) + 2.0 * sizeof(T)), g_capturing);
+      return DCG_OK;
+    }
+  }
+  if constexpr (sizeof(T) == 8) {
+    if (L.fdm) {
+      const size_t smem_f = fdm_smem_bytes(L);
+      const int lm = L.fdm_lmax;
+      if constexpr (D == 2) {
+        if (lm <= 4) k_ras_fdm<D, 4><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        else if (lm <= 6) k_ras_fdm<D, 6><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        else if (lm <= 8) k_ras_fdm<D, 8><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        else if (lm <= 10) k_ras_fdm<D, 10><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        else if (lm <= 12) k_ras_fdm<D, 12><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        else k_ras_fdm<D, 16><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+      } else {
+        if (lm <= 4) k_ras_fdm<D, 4><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        else k_ras_fdm<D, 6><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+      }
+      DCG_LAUNCH_CHECK();
+      prof_end(p, prof, s, L.fdm_flops, bytes, g_capturing);
       prof = prof_begin(p, PC_RAS_UPDATE, s, g_capturing);
       k_ras_update<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(L.d_ysrc, (const T*)L.y, (T*)L.z, L.nn,
                                                                     p->opts.ras_weights == DCG_RAS_RESTRICTED);
@@ -1715,6 +1978,14 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
   DCG_TRY(set_ras_smem(k_ras_solve<float, 3, true>));
   DCG_TRY(set_ras_smem(k_ras_solve<float, 2, false>));
   DCG_TRY(set_ras_smem(k_ras_solve<float, 3, false>));
+  DCG_TRY(set_ras_smem(k_ras_fdm<2, 4>));
+  DCG_TRY(set_ras_smem(k_ras_fdm<2, 6>));
+  DCG_TRY(set_ras_smem(k_ras_fdm<2, 8>));
+  DCG_TRY(set_ras_smem(k_ras_fdm<2, 10>));
+  DCG_TRY(set_ras_smem(k_ras_fdm<2, 12>));
+  DCG_TRY(set_ras_smem(k_ras_fdm<2, 16>));
+  DCG_TRY(set_ras_smem(k_ras_fdm<3, 4>));
+  DCG_TRY(set_ras_smem(k_ras_fdm<3, 6>));
   DCG_TRY(set_ras_smem(k_ras_solve<double, 2, true>));
   DCG_TRY(set_ras_smem(k_ras_solve<double, 3, true>));
   DCG_TRY(set_ras_smem(k_ras_solve<double, 2, false>));

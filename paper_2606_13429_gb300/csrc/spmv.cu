@@ -16,6 +16,7 @@
 //   out = y / f - y / V^T y (only the d diagonal-component rows are computed:
 //   g = V^T A x reads half (2D) or a third (3D) of the matrix).
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace dcg {
 namespace {
@@ -199,6 +200,203 @@ __global__ void k_spmv(SpmvArgs A) {
   if (DOT) grid_reduce<1>(part, A.red);
 }
 
+
+// ---------------------------------------------------------------------------
+// 2D product with the matrix staged in shared memory by bulk copies.
+//
+// A persistent CTA walks tiles of kTR = 32 * RG consecutive block rows. The
+// values of a tile (9 blocks of 128 bytes per interior block row) arrive by
+// one cp.async.bulk per block row into a padded slot of kSlot bytes (the
+// 16-byte pad staggers consecutive rows over the shared-memory banks), and
+// the tile's column indices by one more copy; NS tiles are in flight, each
+// completing on its own mbarrier. Warp w computes scalar row R = w % 4 of 32
+// block rows (lane = block row), so the structural zeros of the 4 x 4 block
+// (10 of 16 entries) are skipped without divergence; x is read through L1.
+// The tile's outputs are gathered in shared memory and written coalesced,
+// with the fused epilogue (f - y, V^T y, dot products) in that pass.
+// ---------------------------------------------------------------------------
+constexpr int kSlot = 9 * 128 + 16;  // bytes per block-row slot (9 blocks + pad)
+
+template <int RG, int NS>
+struct Spmv2Smem {
+  static constexpr int kTR = 32 * RG;
+  static constexpr int kColInts = kTR * 9 + 8;  // column range of a tile, 16-byte aligned start
+  static constexpr size_t kVals = (size_t)kTR * kSlot;
+  static constexpr size_t kStage = kVals + sizeof(int) * kColInts;
+  static constexpr size_t kBytes = NS * kStage + sizeof(double) * kTR * 4;
+};
+
+template <int R, int XM>
+__device__ __forceinline__ double block_row_2d(const double2* vs, const SpmvArgs& A, long long c) {
+  constexpr int k = R / 2, i = R % 2;
+  const double2 va = vs[0], vb = vs[1];
+  const double v[4] = {va.x, va.y, vb.x, vb.y};
+  double xv[4];
+  if (XM == XM_VZ) {
+    const double zz = __dmul_rn(A.isd, __ldg(A.zh + c));
+    xv[0] = zz; xv[1] = 0.0; xv[2] = 0.0; xv[3] = zz;
+  } else {
+    const double2* x2 = reinterpret_cast<const double2*>(A.x + c * 4);
+    const double2 xa = __ldg(x2), xb = __ldg(x2 + 1);
+    xv[0] = xa.x; xv[1] = xa.y; xv[2] = xb.x; xv[3] = xb.y;
+  }
+  double acc;
+  if (k == i) {
+    acc = v[0] * xv[0];
+    acc = fma(v[3], xv[3], acc);
+    acc = fma(v[k * 2 + (1 - k)], xv[k * 2 + (1 - k)], acc);
+  } else {
+    acc = v[k * 2] * xv[k * 2];
+    acc = fma(v[k * 2 + 1], xv[k * 2 + 1], acc);
+  }
+  return acc;
+}
+
+template <int R, int XM>
+__device__ __forceinline__ double row_from_smem(const unsigned char* slot, const int* cols, int nb,
+                                                const SpmvArgs& A) {
+  double acc = 0.0;
+#pragma unroll 3
+  for (int j = 0; j < nb; ++j) {
+    const double2* vs = reinterpret_cast<const double2*>(slot + j * 128 + R * 32);
+    acc += block_row_2d<R, XM>(vs, A, cols[j]);
+  }
+  return acc;
+}
+
+template <int XM, int OM, bool DOT, int RG, int NS>
+__global__ void __launch_bounds__(128 * RG) k_spmv2_tma(SpmvArgs A, long long ntiles, double* err) {
+  using L = Spmv2Smem<RG, NS>;
+  constexpr int TR = L::kTR;
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ __align__(8) uint64_t full[NS];
+  double* ys = reinterpret_cast<double*>(sm + NS * L::kStage);  // [TR][4]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long nn = A.n_nodes;
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) mbar_init(&full[s], 1);
+  }
+  __syncthreads();
+  // warp 0 issues the copies of tile `t` into stage `s` (the stage's earlier
+  // contents were read by all threads before the barrier that precedes this)
+  auto issue = [&](long long t, int s) {
+    fence_async_smem();
+    const long long a0 = t * TR;
+    const long long a1 = min(a0 + TR, nn);
+    unsigned char* vals_s = sm + s * L::kStage;
+    int* cols_s = reinterpret_cast<int*>(vals_s + L::kVals);
+    const int c0 = __ldg(A.row_ptr + a0), c1 = __ldg(A.row_ptr + a1);
+    const int c0a = c0 & ~3;
+    const unsigned cbytes = (unsigned)(((c1 - c0a) * 4 + 15) & ~15);
+    if (lane == 0) {
+      const unsigned vbytes = (unsigned)(c1 - c0) * 128u;
+      mbar_expect_tx(&full[s], vbytes + cbytes);
+      tma_load_1d(cols_s, A.col_idx + c0a, cbytes, &full[s]);
+    }
+    __syncwarp();
+    for (long long a = a0 + lane; a < a1; a += 32) {
+      const int j0 = __ldg(A.row_ptr + a), j1 = __ldg(A.row_ptr + a + 1);
+      tma_load_1d(vals_s + (a - a0) * kSlot, A.vals + (long long)j0 * 16, (unsigned)(j1 - j0) * 128u, &full[s]);
+    }
+  };
+  long long t = blockIdx.x;
+  int nissued = 0;  // tiles whose copies this CTA has issued
+  if (warp == 0) {
+    for (int s = 0; s < NS; ++s)
+      if (t + (long long)s * gridDim.x < ntiles) issue(t + (long long)s * gridDim.x, s);
+  }
+  for (int s = 0; s < NS; ++s)
+    if (t + (long long)s * gridDim.x < ntiles) ++nissued;
+  double part[1] = {0.0};
+  bool failed = false;
+  int k = 0;
+  for (; t < ntiles; ++k, t += gridDim.x) {
+    const int s = k % NS;
+    const unsigned phase = (unsigned)(k / NS) & 1u;
+    const bool ok = mbar_wait_bounded(&full[s], phase) || mbar_wait_bounded(&full[s], phase);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const long long a0 = t * TR;
+    const unsigned char* vals_s = sm + s * L::kStage;
+    const int* cols_s = reinterpret_cast<const int*>(vals_s + L::kVals);
+    const int c0a = __ldg(A.row_ptr + a0) & ~3;
+    {
+      const int r = (warp >> 2) * 32 + lane;
+      const long long a = a0 + r;
+      double acc = 0.0;
+      if (a < nn) {
+        const int j0 = __ldg(A.row_ptr + a), j1 = __ldg(A.row_ptr + a + 1);
+        const unsigned char* slot = vals_s + r * kSlot;
+        const int* cols = cols_s + (j0 - c0a);
+        switch (warp & 3) {
+          case 0: acc = row_from_smem<0, XM>(slot, cols, j1 - j0, A); break;
+          case 1: acc = row_from_smem<1, XM>(slot, cols, j1 - j0, A); break;
+          case 2: acc = row_from_smem<2, XM>(slot, cols, j1 - j0, A); break;
+          default: acc = row_from_smem<3, XM>(slot, cols, j1 - j0, A); break;
+        }
+      }
+      ys[r * 4 + (warp & 3)] = acc;
+    }
+    __syncthreads();  // stage s consumed, ys complete
+    if (t + (long long)NS * gridDim.x < ntiles) {
+      if (warp == 0) issue(t + (long long)NS * gridDim.x, s);
+      ++nissued;
+    }
+    // coalesced output pass: thread e writes element a0*4 + e of the tile
+    const long long e_end = min((long long)TR * 4, (nn - a0) * 4);
+    for (int e = tid; e < e_end; e += blockDim.x) {
+      const long long row = a0 * 4 + e;
+      const double v = ys[e];
+      if (OM == OM_FMY) {
+        const double out = __dsub_rn(A.f[row], v);
+        A.y[row] = out;
+        if (DOT) part[0] = fma(out, out, part[0]);
+      } else {
+        A.y[row] = v;
+        if (DOT && OM == OM_Y) part[0] = fma(A.dvec[row], v, part[0]);
+      }
+    }
+    if (OM == OM_YVT) {
+      for (int r = tid; r < TR && a0 + r < nn; r += blockDim.x) {
+        const double g = (ys[r * 4] + ys[r * 4 + 3]) * A.isd;
+        A.g[a0 + r] = g;
+        if (DOT) part[0] = fma(g, g, part[0]);
+      }
+    }
+    __syncthreads();  // ys reused by the next tile
+  }
+  if (failed) {
+    // a wait gave up: record it, and wait (again bounded) for the copies still
+    // in flight into this CTA's shared memory before leaving
+    if (tid == 0) *err = 1.0;
+    for (int kk = k; kk < nissued; ++kk) {
+      const int s = kk % NS;
+      mbar_wait_bounded(&full[s], (unsigned)(kk / NS) & 1u);
+    }
+    __syncthreads();
+  }
+  if (DOT) grid_reduce<1>(part, A.red);
+}
+
+template <int XM, int OM, bool DOT>
+void launch_spmv2_tma(const SpmvArgs& a, double* err, cudaStream_t s) {
+  constexpr int RG = 2, NS = 2;
+  using L = Spmv2Smem<RG, NS>;
+  const long long ntiles = (a.n_nodes + L::kTR - 1) / L::kTR;
+  const int grid = (int)std::min<long long>(ntiles, 152);
+  k_spmv2_tma<XM, OM, DOT, RG, NS><<<grid, 128 * RG, L::kBytes, s>>>(a, ntiles, err);
+}
+
+template <int XM, int OM, bool DOT>
+int set_spmv2_smem() {
+  using L = Spmv2Smem<2, 2>;
+  DCG_CUDA(cudaFuncSetAttribute(k_spmv2_tma<XM, OM, DOT, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)L::kBytes));
+  return DCG_OK;
+}
+
 // w = x - V zh (node-major, the d diagonal components of each node shifted):
 // formed once per node instead of once per stored block that reads it, which
 // keeps the FP64 arithmetic of the deflated product at that of A x
@@ -236,7 +434,15 @@ int launch(dcg_problem* p, SpmvArgs a, cudaStream_t s, bool lowp = false) {
   if (OM == OM_YVT) bytes += nn * 8.0;                  // g
   if (OM == OM_FMY) bytes += N * 8.0;                   // f
   const int prof = prof_begin(p, PC_SPMV, s);
-  if (p->dim == 2) {
+  bool staged = false;
+  if constexpr (OM != OM_VT && XM != XM_X_MINUS_VZ) {
+    if (p->dim == 2) {
+      launch_spmv2_tma<XM, OM, DOT>(a, p->scal + S_ERR, s);
+      staged = true;
+    }
+  }
+  if (staged) {
+  } else if (p->dim == 2) {
     const int threads = 32 * (OM == OM_VT ? 2 : 4);
     k_spmv<2, XM, OM, DOT><<<grid, threads, 0, s>>>(a);
   } else {
@@ -249,6 +455,18 @@ int launch(dcg_problem* p, SpmvArgs a, cudaStream_t s, bool lowp = false) {
 }
 
 }  // namespace
+
+int spmv_init(dcg_problem* p) {
+  if (p->dim != 2 || p->matrix_free) return DCG_OK;
+  // opt-in of the staged 2D products into their shared memory (per device)
+  DCG_TRY((set_spmv2_smem<XM_X, OM_Y, false>()));
+  DCG_TRY((set_spmv2_smem<XM_X, OM_Y, true>()));
+  DCG_TRY((set_spmv2_smem<XM_X, OM_FMY, true>()));
+  DCG_TRY((set_spmv2_smem<XM_X, OM_YVT, true>()));
+  DCG_TRY((set_spmv2_smem<XM_VZ, OM_Y, false>()));
+  DCG_TRY((set_spmv2_smem<XM_VZ, OM_FMY, true>()));
+  return DCG_OK;
+}
 
 int spmv_plain(dcg_problem* p, const double* x, double* y, cudaStream_t s, bool lowp) {
   SpmvArgs a{};

@@ -69,7 +69,7 @@ def test_coarse_solve_long_transforms(d, n, levels):
     passes), against a sparse LU of the Galerkin coarse matrix P^T Z_J P,
     Z_J = L / d (Corollary 1), element by element."""
     prob = dcg.dcg_assemble(d, n, 1e-4)
-    dcg.dcg_setup(prob, dcg.options(max_levels=levels, patch=8, overlap=2))
+    dcg.dcg_setup(prob, dcg.options(max_levels=levels, patch=8 if d == 2 else 4, overlap=2 if d == 2 else 1))
     sizes = mg.level_sizes(n, levels)
     mc = sizes[-1] - 1
     ZJ = fem.laplacian_kron(d, n) / d
