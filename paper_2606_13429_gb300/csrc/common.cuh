@@ -1,6 +1,7 @@
 // Common device helpers and the problem object of libdcg.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <atomic>
 #include <cstdint>
@@ -265,6 +266,7 @@ struct dcg_problem {
   int* row_ptr = nullptr;
   int* col_idx = nullptr;
   double* vals = nullptr;
+  CUtensorMap vals_map{};          // 2D products: the values as a TMA tensor (spmv.cu)
   double* inv_nu_elem = nullptr;   // per-element 1/nu (device, matrix-free or assembly)
   // scratch for reductions
   double* partials = nullptr;

@@ -188,8 +188,9 @@ def test_fcg1_breakdown_and_fcg_inf_robustness():
     prob = dcg.dcg_assemble(2, 12, 0.1)
     res = {}
     for rec in ("fcg1", "fcg_inf"):
+        # fcg_max_dirs = 400 >= max_it: the untruncated FCG(inf) of Algorithm 1
         dcg.dcg_setup(prob, gpu_opts(o, recurrence=dcg.DCG_FCG1 if rec == "fcg1" else dcg.DCG_FCG_INF,
-                                     inner_rule=dcg.DCG_INNER_ADAPTIVE, c=0.2, max_restarts=0))
+                                     inner_rule=dcg.DCG_INNER_ADAPTIVE, c=0.2, max_restarts=0, fcg_max_dirs=400))
         x = torch.zeros(prob.N, dtype=torch.float64, device="cuda")
         res[rec] = dcg.dcg_solve(prob, dev(f), x, tol=1e-8, max_it=400)
     _, s1 = solvers.FDCG(asm, solvers.FDCGOptions(mg=o, recurrence="fcg1", inner_rule="adaptive", c=0.2,
