@@ -242,8 +242,6 @@ int dcg_assemble(const dcg_mesh* mesh, double dt, double nu, const double* nu_el
   }
   st = assemble_device(p, nu_elem, s);
   if (st != DCG_OK) return fail(st);
-  st = spmv_init(p);
-  if (st != DCG_OK) return fail(st);
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     set_error("dcg_assemble", cudaGetLastError());
     return fail(DCG_ERR_CUDA);

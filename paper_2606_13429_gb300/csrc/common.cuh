@@ -1,7 +1,6 @@
 // Common device helpers and the problem object of libdcg.
 #pragma once
 
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <atomic>
 #include <cstdint>
@@ -266,7 +265,6 @@ struct dcg_problem {
   int* row_ptr = nullptr;
   int* col_idx = nullptr;
   double* vals = nullptr;
-  CUtensorMap vals_map{};          // 2D products: the values as a TMA tensor (spmv.cu)
   double* inv_nu_elem = nullptr;   // per-element 1/nu (device, matrix-free or assembly)
   // scratch for reductions
   double* partials = nullptr;
@@ -317,8 +315,6 @@ void prof_clear_graph(dcg_problem* p);
 
 // launchers implemented in the .cu files
 int assemble_device(dcg_problem* p, const double* nu_elem_host, cudaStream_t s);
-// per-device kernel attributes of the BSR products (called by dcg_assemble)
-int spmv_init(dcg_problem* p);
 int spmv_plain(dcg_problem* p, const double* x, double* y, cudaStream_t s, bool lowp = false);
 // y = A x with dot(dv, y) into scal[slot] when dv != nullptr
 int spmv_dot(dcg_problem* p, const double* x, double* y, const double* dv, int slot, cudaStream_t s);

@@ -43,6 +43,8 @@ namespace dcg {
 namespace {
 
 constexpr int kKC = 32;       // K chunk of the inverse staged in shared memory
+constexpr int kFdmBatch = 16; // boxes per work item of the fast-diagonalisation smoother
+constexpr int kFdmThreads = 192;
 constexpr int kRasThreads = 256;
 constexpr int kMaxNp = 256;   // largest box (nodes) supported
 
@@ -715,7 +717,7 @@ __device__ __forceinline__ void fdm_line_solve(double* __restrict__ W, int base,
 }
 
 template <int D, int LM>
-__global__ void __launch_bounds__(128) k_ras_fdm(RasArgs ra, const double* __restrict__ rvec,
+__global__ void __launch_bounds__(kFdmThreads) k_ras_fdm(RasArgs ra, const double* __restrict__ rvec,
                                                  const double* __restrict__ tab, double* __restrict__ y) {
   extern __shared__ __align__(16) double W[];
   const int w = blockIdx.x;
@@ -1326,6 +1328,21 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
     pclass[pid] = c;
   }
 
+  // FP64 levels whose stencil is the Q1 Laplacian / d solve their boxes by
+  // fast diagonalisation (tables built below), in work items of kFdmBatch boxes
+  L.fdm = false;
+  if (!fp32) {
+    int lmax = 0;
+    for (int t = 0; t < nt; ++t) lmax = std::max(lmax, len1[t]);
+    const Stencil<double> cf = q1_laplacian_over_d(D, 1.0 / L.n);
+    double dev = 0.0, mx = 0.0;
+    for (int k = 0; k < 27; ++k) {
+      dev = std::max(dev, std::fabs(cf.c[k] - L.st64.c[k]));
+      mx = std::max(mx, std::fabs(cf.c[k]));
+    }
+    L.fdm = dev <= 1e-12 * mx && lmax <= (D == 2 ? 16 : 6);
+    L.fdm_lmax = lmax;
+  }
   L.ras_np2 = 0;
   for (int pid = 0; pid < L.npatch; ++pid) L.ras_np2 += (long long)L.classes[pclass[pid]].np * L.classes[pclass[pid]].np;
   L.nclass = (int)L.classes.size();
@@ -1340,7 +1357,7 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
     c.npk = (c.np + 15) / 16 * 16;   // tensor-core N and K padding
     c.inv_off = inv_total;           // 16-byte aligned for the bulk copy into shared memory
     inv_total += L.tc ? (long long)c.npk * c.npk : (long long)c.np * c.npp;
-    c.nb = L.tc ? 128 : class_batch(c.np);
+    c.nb = L.tc ? 128 : (L.fdm ? kFdmBatch : class_batch(c.np));
     L.npmax = std::max(L.npmax, c.np);
     L.gmax = std::max(L.gmax, (long long)c.np * c.nb);
   }
@@ -1454,22 +1471,11 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
   DCG_CUDA(cudaMemcpyAsync(L.d_work, work.data(), sizeof(int) * work.size(), cudaMemcpyHostToDevice, s));
   DCG_CUDA(cudaMemcpyAsync(L.d_classes, L.classes.data(), sizeof(RasClass) * L.nclass, cudaMemcpyHostToDevice, s));
   const size_t tsz = fp32 ? sizeof(float) : sizeof(double);
-  // FP64 levels whose stencil is the Q1 Laplacian / d: local solves by fast
-  // diagonalisation (sine matrices per box extent, elimination factors of the
-  // line solves along the last axis), computed here in FP64
-  L.fdm = false;
-  if (!fp32) {
-    int lmax = 0;
-    for (const auto& c : L.classes)
-      for (int k = 0; k < D; ++k) lmax = std::max(lmax, c.len[k]);
+  // fast-diagonalisation tables (sine matrices per box extent, elimination
+  // factors of the line solves along the last axis), computed here in FP64
+  if (L.fdm) {
     const double h = 1.0 / L.n;
-    const Stencil<double> cf = q1_laplacian_over_d(D, h);
-    double dev = 0.0, mx = 0.0;
-    for (int k = 0; k < 27; ++k) {
-      dev = std::max(dev, std::fabs(cf.c[k] - L.st64.c[k]));
-      mx = std::max(mx, std::fabs(cf.c[k]));
-    }
-    if (dev <= 1e-12 * mx && lmax <= (D == 2 ? 16 : 6)) {
+    {
       std::vector<double> tab;
       std::map<int, int> s_off;  // extent -> offset of its sine matrix
       auto sine = [&](int l) {
@@ -1518,8 +1524,6 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
       DCG_CUDA(cudaMemcpyAsync(L.d_fdm, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s));
       DCG_CUDA(cudaMemcpyAsync(L.d_classes, L.classes.data(), sizeof(RasClass) * L.nclass, cudaMemcpyHostToDevice, s));
       DCG_CUDA(cudaStreamSynchronize(s));  // the host table goes out of scope
-      L.fdm = true;
-      L.fdm_lmax = lmax;
       // algorithmic flops of one smoothing product (an FMA counts 2): folded
       // transforms along every axis but the last, forward and back, and the
       // line solves along the last
@@ -1682,15 +1686,15 @@ int ras_step_t(dcg_problem* p, Level& L, cudaStream_t s, bool z_zero = false) {
       const size_t smem_f = fdm_smem_bytes(L);
       const int lm = L.fdm_lmax;
       if constexpr (D == 2) {
-        if (lm <= 4) k_ras_fdm<D, 4><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
-        else if (lm <= 6) k_ras_fdm<D, 6><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
-        else if (lm <= 8) k_ras_fdm<D, 8><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
-        else if (lm <= 10) k_ras_fdm<D, 10><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
-        else if (lm <= 12) k_ras_fdm<D, 12><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
-        else k_ras_fdm<D, 16><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        if (lm <= 4) k_ras_fdm<D, 4><<<L.nwork, kFdmThreads, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        else if (lm <= 6) k_ras_fdm<D, 6><<<L.nwork, kFdmThreads, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        else if (lm <= 8) k_ras_fdm<D, 8><<<L.nwork, kFdmThreads, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        else if (lm <= 10) k_ras_fdm<D, 10><<<L.nwork, kFdmThreads, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        else if (lm <= 12) k_ras_fdm<D, 12><<<L.nwork, kFdmThreads, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        else k_ras_fdm<D, 16><<<L.nwork, kFdmThreads, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
       } else {
-        if (lm <= 4) k_ras_fdm<D, 4><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
-        else k_ras_fdm<D, 6><<<L.nwork, 128, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        if (lm <= 4) k_ras_fdm<D, 4><<<L.nwork, kFdmThreads, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
+        else k_ras_fdm<D, 6><<<L.nwork, kFdmThreads, smem_f, s>>>(ra, (const double*)rvec, L.d_fdm, (double*)L.y);
       }
       DCG_LAUNCH_CHECK();
       prof_end(p, prof, s, L.fdm_flops, bytes, g_capturing);

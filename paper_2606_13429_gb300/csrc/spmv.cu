@@ -16,9 +16,6 @@
 //   out = y / f - y / V^T y (only the d diagonal-component rows are computed:
 //   g = V^T A x reads half (2D) or a third (3D) of the matrix).
 #include "common.cuh"
-#include "tma.cuh"
-
-#include <cuda.h>
 
 namespace dcg {
 namespace {
@@ -203,241 +200,6 @@ __global__ void k_spmv(SpmvArgs A) {
 }
 
 
-// ---------------------------------------------------------------------------
-// 2D product with the matrix staged in shared memory by TMA.
-//
-// A persistent CTA walks tiles of kTR = 32 * RG consecutive block rows. The
-// tile's blocks (at most 9 per block row, contiguous in the BSR arrays) arrive
-// as kCopies tensor copies of kBox blocks each (the matrix viewed as a 2D
-// tensor of 16 doubles x nnzb blocks, copied with the 128-byte swizzle: the
-// 16-byte chunk c of smem row r lands at chunk c ^ (r mod 8)), and the tile's
-// column indices by one bulk copy; NS tiles are in flight, each completing on
-// its own mbarrier. Warp w computes scalar row R = w % 4 of 32 block rows
-// (lane = block row), so the structural zeros of the 4 x 4 block (10 of 16
-// entries) are skipped without divergence; consecutive lanes read blocks
-// about 9 rows apart, which the swizzle spreads over all eight 16-byte chunk
-// positions (conflict-free 16-byte shared loads). x is read through L1. The
-// tile's outputs are gathered in shared memory and written coalesced, with
-// the fused epilogue (f - y, V^T y, dot products) in that pass.
-// ---------------------------------------------------------------------------
-template <int RG, int NS>
-struct Spmv2Smem {
-  static constexpr int kTR = 32 * RG;
-  static constexpr int kBox = 3 * kTR;                    // blocks per tensor copy (<= 256)
-  static constexpr int kCopies = 3;                       // 9 * kTR blocks per tile at most
-  static constexpr int kColInts = kTR * 9 + 8;            // column range, 16-byte aligned start
-  static constexpr size_t kVals = (size_t)kCopies * kBox * 128;
-  static constexpr size_t kStage = (kVals + sizeof(int) * kColInts + 1023) / 1024 * 1024;
-  static constexpr size_t kBytes = NS * kStage + sizeof(double) * kTR * 4 + 1024;  // + alignment slack
-};
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-template <int R, int XM>
-__device__ __forceinline__ double block_row_2d(const unsigned char* row, int sw, const SpmvArgs& A, long long c) {
-  constexpr int k = R / 2, i = R % 2;
-  // chunks 2R and 2R + 1 of the swizzled 128-byte row
-  const double2 va = *reinterpret_cast<const double2*>(row + (((2 * R) ^ sw) << 4));
-  const double2 vb = *reinterpret_cast<const double2*>(row + (((2 * R + 1) ^ sw) << 4));
-  const double v[4] = {va.x, va.y, vb.x, vb.y};
-  double xv[4];
-  if (XM == XM_VZ) {
-    const double zz = __dmul_rn(A.isd, __ldg(A.zh + c));
-    xv[0] = zz; xv[1] = 0.0; xv[2] = 0.0; xv[3] = zz;
-  } else {
-    const double2* x2 = reinterpret_cast<const double2*>(A.x + c * 4);
-    const double2 xa = __ldg(x2), xb = __ldg(x2 + 1);
-    xv[0] = xa.x; xv[1] = xa.y; xv[2] = xb.x; xv[3] = xb.y;
-  }
-  double acc;
-  if (k == i) {
-    acc = v[0] * xv[0];
-    acc = fma(v[3], xv[3], acc);
-    acc = fma(v[k * 2 + (1 - k)], xv[k * 2 + (1 - k)], acc);
-  } else {
-    acc = v[k * 2] * xv[k * 2];
-    acc = fma(v[k * 2 + 1], xv[k * 2 + 1], acc);
-  }
-  return acc;
-}
-
-template <int R, int XM>
-__device__ __forceinline__ double row_from_smem(const unsigned char* vals, int r0, const int* cols, int nb,
-                                                const SpmvArgs& A) {
-  double acc = 0.0;
-#pragma unroll 3
-  for (int j = 0; j < nb; ++j) {
-    const int r = r0 + j;  // smem row of the block
-    acc += block_row_2d<R, XM>(vals + r * 128, r & 7, A, cols[j]);
-  }
-  return acc;
-}
-
-template <int XM, int OM, bool DOT, int RG, int NS>
-__global__ void __launch_bounds__(128 * RG) k_spmv2_tma(const __grid_constant__ CUtensorMap tmap, SpmvArgs A,
-                                                        long long ntiles, double* err) {
-  using L = Spmv2Smem<RG, NS>;
-  constexpr int TR = L::kTR;
-  extern __shared__ __align__(1024) unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t full[NS];
-  // the 128-byte swizzle repeats every 1024 bytes: stage bases 1024-aligned
-  unsigned char* sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
-  double* ys = reinterpret_cast<double*>(sm + NS * L::kStage);  // [TR][4]
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long nn = A.n_nodes;
-  if (tid == 0) {
-    for (int s = 0; s < NS; ++s) mbar_init(&full[s], 1);
-  }
-  __syncthreads();
-  // thread 0 issues the copies of tile `t` into stage `s` (the stage's earlier
-  // contents were read by all threads before the barrier that precedes this)
-  auto issue = [&](long long t, int s) {
-    fence_async_smem();
-    const long long a0 = t * TR;
-    const long long a1 = min(a0 + TR, nn);
-    unsigned char* vals_s = sm + s * L::kStage;
-    int* cols_s = reinterpret_cast<int*>(vals_s + L::kVals);
-    const int c0 = __ldg(A.row_ptr + a0), c1 = __ldg(A.row_ptr + a1);
-    const int c0a = c0 & ~3;
-    const unsigned cbytes = (unsigned)(((c1 - c0a) * 4 + 15) & ~15);
-    mbar_expect_tx(&full[s], (unsigned)L::kVals + cbytes);
-    for (int k = 0; k < L::kCopies; ++k) tma_load_2d(vals_s + k * L::kBox * 128, &tmap, 0, c0 + k * L::kBox, &full[s]);
-    tma_load_1d(cols_s, A.col_idx + c0a, cbytes, &full[s]);
-  };
-  long long t = blockIdx.x;
-  int nissued = 0;  // tiles whose copies this CTA has issued (every thread counts)
-  for (int s = 0; s < NS; ++s) {
-    if (t + (long long)s * gridDim.x < ntiles) {
-      if (tid == 0) issue(t + (long long)s * gridDim.x, s);
-      ++nissued;
-    }
-  }
-  double part[1] = {0.0};
-  bool failed = false;
-  int k = 0;
-  for (; t < ntiles; ++k, t += gridDim.x) {
-    const int s = k % NS;
-    const unsigned phase = (unsigned)(k / NS) & 1u;
-    const bool ok = mbar_wait_bounded(&full[s], phase) || mbar_wait_bounded(&full[s], phase);
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    const long long a0 = t * TR;
-    const unsigned char* vals_s = sm + s * L::kStage;
-    const int* cols_s = reinterpret_cast<const int*>(vals_s + L::kVals);
-    const int c0 = __ldg(A.row_ptr + a0);
-    const int c0a = c0 & ~3;
-    {
-      const int r = (warp >> 2) * 32 + lane;
-      const long long a = a0 + r;
-      double acc = 0.0;
-      if (a < nn) {
-        const int j0 = __ldg(A.row_ptr + a), j1 = __ldg(A.row_ptr + a + 1);
-        const int* cols = cols_s + (j0 - c0a);
-        switch (warp & 3) {
-          case 0: acc = row_from_smem<0, XM>(vals_s, j0 - c0, cols, j1 - j0, A); break;
-          case 1: acc = row_from_smem<1, XM>(vals_s, j0 - c0, cols, j1 - j0, A); break;
-          case 2: acc = row_from_smem<2, XM>(vals_s, j0 - c0, cols, j1 - j0, A); break;
-          default: acc = row_from_smem<3, XM>(vals_s, j0 - c0, cols, j1 - j0, A); break;
-        }
-      }
-      ys[r * 4 + (warp & 3)] = acc;
-    }
-    __syncthreads();  // stage s consumed, ys complete
-    if (t + (long long)NS * gridDim.x < ntiles) {
-      if (tid == 0) issue(t + (long long)NS * gridDim.x, s);
-      ++nissued;
-    }
-    // coalesced output pass: thread e writes element a0*4 + e of the tile
-    const long long e_end = min((long long)TR * 4, (nn - a0) * 4);
-    for (int e = tid; e < e_end; e += blockDim.x) {
-      const long long row = a0 * 4 + e;
-      const double v = ys[e];
-      if (OM == OM_FMY) {
-        const double out = __dsub_rn(A.f[row], v);
-        A.y[row] = out;
-        if (DOT) part[0] = fma(out, out, part[0]);
-      } else {
-        A.y[row] = v;
-        if (DOT && OM == OM_Y) part[0] = fma(A.dvec[row], v, part[0]);
-      }
-    }
-    if (OM == OM_YVT) {
-      for (int r = tid; r < TR && a0 + r < nn; r += blockDim.x) {
-        const double g = (ys[r * 4] + ys[r * 4 + 3]) * A.isd;
-        A.g[a0 + r] = g;
-        if (DOT) part[0] = fma(g, g, part[0]);
-      }
-    }
-    __syncthreads();  // ys reused by the next tile
-  }
-  if (failed) {
-    // a wait gave up: record it, and wait (again bounded) for the copies still
-    // in flight into this CTA's shared memory before leaving
-    if (tid == 0) *err = 1.0;
-    for (int kk = k; kk < nissued; ++kk) mbar_wait_bounded(&full[kk % NS], (unsigned)(kk / NS) & 1u);
-    __syncthreads();
-  }
-  if (DOT) grid_reduce<1>(part, A.red);
-}
-
-constexpr int kSpmvRG = 2, kSpmvNS = 2;
-
-template <int XM, int OM, bool DOT>
-void launch_spmv2_tma(const CUtensorMap& tmap, const SpmvArgs& a, double* err, cudaStream_t s) {
-  using L = Spmv2Smem<kSpmvRG, kSpmvNS>;
-  const long long ntiles = (a.n_nodes + L::kTR - 1) / L::kTR;
-  const int grid = (int)std::min<long long>(ntiles, 152);
-  k_spmv2_tma<XM, OM, DOT, kSpmvRG, kSpmvNS><<<grid, 128 * kSpmvRG, L::kBytes, s>>>(tmap, a, ntiles, err);
-}
-
-template <int XM, int OM, bool DOT>
-int set_spmv2_smem() {
-  using L = Spmv2Smem<kSpmvRG, kSpmvNS>;
-  DCG_CUDA(cudaFuncSetAttribute(k_spmv2_tma<XM, OM, DOT, kSpmvRG, kSpmvNS>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kBytes));
-  return DCG_OK;
-}
-
-// Tensor map of the BSR values as a 2D tensor [nnzb][16] doubles with boxes
-// of kBox blocks and the 128-byte swizzle (cuTensorMapEncodeTiled, looked up
-// through the runtime so the library needs no link against the driver).
-int make_vals_tensor_map(dcg_problem* p) {
-  using L = Spmv2Smem<kSpmvRG, kSpmvNS>;
-  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static EncodeFn encode = nullptr;
-  if (!encode) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q{};
-    DCG_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-    if (!fn || q != cudaDriverEntryPointSuccess) {
-      set_error_msg("cuTensorMapEncodeTiled is not available from the driver");
-      return DCG_ERR_CUDA;
-    }
-    encode = reinterpret_cast<EncodeFn>(fn);
-  }
-  const cuuint64_t dims[2] = {16, (cuuint64_t)p->nnzb};
-  const cuuint64_t strides[1] = {128};
-  const cuuint32_t box[2] = {16, (cuuint32_t)L::kBox};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode(&p->vals_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, p->vals, dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    set_error_msg("cuTensorMapEncodeTiled failed for the BSR values");
-    return DCG_ERR_CUDA;
-  }
-  return DCG_OK;
-}
-
 // w = x - V zh (node-major, the d diagonal components of each node shifted):
 // formed once per node instead of once per stored block that reads it, which
 // keeps the FP64 arithmetic of the deflated product at that of A x
@@ -475,15 +237,7 @@ int launch(dcg_problem* p, SpmvArgs a, cudaStream_t s, bool lowp = false) {
   if (OM == OM_YVT) bytes += nn * 8.0;                  // g
   if (OM == OM_FMY) bytes += N * 8.0;                   // f
   const int prof = prof_begin(p, PC_SPMV, s);
-  bool staged = false;
-  if constexpr (OM != OM_VT && XM != XM_X_MINUS_VZ) {
-    if (p->dim == 2) {
-      launch_spmv2_tma<XM, OM, DOT>(p->vals_map, a, p->scal + S_ERR, s);
-      staged = true;
-    }
-  }
-  if (staged) {
-  } else if (p->dim == 2) {
+  if (p->dim == 2) {
     const int threads = 32 * (OM == OM_VT ? 2 : 4);
     k_spmv<2, XM, OM, DOT><<<grid, threads, 0, s>>>(a);
   } else {
@@ -496,19 +250,6 @@ int launch(dcg_problem* p, SpmvArgs a, cudaStream_t s, bool lowp = false) {
 }
 
 }  // namespace
-
-int spmv_init(dcg_problem* p) {
-  if (p->dim != 2 || p->matrix_free) return DCG_OK;
-  DCG_TRY(make_vals_tensor_map(p));
-  // opt-in of the staged 2D products into their shared memory (per device)
-  DCG_TRY((set_spmv2_smem<XM_X, OM_Y, false>()));
-  DCG_TRY((set_spmv2_smem<XM_X, OM_Y, true>()));
-  DCG_TRY((set_spmv2_smem<XM_X, OM_FMY, true>()));
-  DCG_TRY((set_spmv2_smem<XM_X, OM_YVT, true>()));
-  DCG_TRY((set_spmv2_smem<XM_VZ, OM_Y, false>()));
-  DCG_TRY((set_spmv2_smem<XM_VZ, OM_FMY, true>()));
-  return DCG_OK;
-}
 
 int spmv_plain(dcg_problem* p, const double* x, double* y, cudaStream_t s, bool lowp) {
   SpmvArgs a{};
@@ -568,6 +309,20 @@ int spmv_defl(dcg_problem* p, const double* x, const double* zh, double* q, int 
 }
 
 int spmv_y_vt(dcg_problem* p, const double* x, double* t, double* g, int slot, cudaStream_t s) {
+  if (p->dim == 2) {
+    // 2D: the plain product (which streams the matrix at the rate of the
+    // lane-per-block-row layout) and the extraction g = V^T t as a separate
+    // pass over t: cheaper than the in-kernel exchange between the warps of
+    // the diagonal-component rows
+    SpmvArgs a{};
+    a.x = x;
+    a.y = t;
+    DCG_TRY((launch<XM_X, OM_Y, false>(p, a, s)));
+    const int prof = prof_begin(p, PC_VEC, s);
+    DCG_TRY(vec_extract(p, t, g, slot, s));
+    prof_end(p, prof, s, 2.0 * p->n_nodes * p->dim, 8.0 * (2.0 * p->n_nodes + p->n_nodes));
+    return DCG_OK;
+  }
   SpmvArgs a{};
   a.x = x;
   a.y = t;
