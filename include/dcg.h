@@ -123,6 +123,18 @@ typedef struct {
                         reconstructed and restarted from its true residual
                         (such restarts do not count against max_restarts);
                         0 = off [200] */
+  int device_loop;   /* deflated CG with W-cycle inner solves on the
+                        assembled operator: 1 = the whole solve is captured
+                        once into a CUDA graph whose loops (restarts, outer
+                        iterations, W-cycles of each inner solve) are
+                        conditional nodes driven by device-side tests, so a
+                        solve is one graph launch with no host round trip per
+                        iteration (re-captured when f, x, tol or max_it
+                        change; kernel-class timing uses the host-driven loop);
+                        a nonzero initial guess is then handled through the
+                        residual equation A e = f - A x0. 0 = host-driven
+                        loop with one convergence read per outer iteration
+                        and per W-cycle [1] */
 } dcg_options;
 
 typedef struct {

@@ -40,7 +40,8 @@ int check_options(const dcg_options* o, int dim) {
             (o->recurrence >= 0 && o->recurrence <= 2) && (o->precision == DCG_FP64 || o->precision == DCG_MIXED) &&
             (o->ras_inverse == DCG_INV_FP32 || o->ras_inverse == DCG_INV_BF16) &&
             (o->ras_weights == 0 || o->ras_weights == 1) && (o->deflate == 0 || o->deflate == 1) &&
-            o->max_restarts >= 0 && o->fcg_max_dirs >= 0 && o->check_every >= 1 && o->stall_window >= 0;
+            o->max_restarts >= 0 && o->fcg_max_dirs >= 0 && o->check_every >= 1 && o->stall_window >= 0 &&
+            (o->device_loop == 0 || o->device_loop == 1);
   if (!ok) {
     set_error_msg("invalid dcg_options field");
     return DCG_ERR_INVALID_ARG;
@@ -167,6 +168,7 @@ void dcg_default_options(dcg_options* o) {
   o->fcg_max_dirs = 0;
   o->check_every = 1;
   o->stall_window = 200;
+  o->device_loop = 1;
 }
 
 const char* dcg_status_string(int s) {
@@ -255,6 +257,7 @@ int dcg_setup(dcg_problem* p, const dcg_options* opts, void* stream) {
   DCG_TRY(check_options(opts, p->dim));
   cudaStream_t s = (cudaStream_t)stream;
   p->is_setup = false;
+  graph_free(p);
   free_solver_buffers(p);
   mg_free(p);
   p->opts = *opts;
@@ -344,6 +347,18 @@ int dcg_solve_batched(int nprob, dcg_problem* const* probs, int nrhs, const doub
       if (!f_dev[i * nrhs + r] || !x_dev[i * nrhs + r]) return DCG_ERR_INVALID_ARG;
   }
   if (nprob == 0) return DCG_OK;
+  bool graph_ok = true;
+  for (int i = 0; i < nprob; ++i) graph_ok = graph_ok && graph_solve_supported(probs[i]);
+  if (graph_ok) {
+    // one CUDA graph for the whole batch: every pair stops at its own
+    // device-side convergence test, problems run as independent branches
+    const int rc = graph_solve_batched(nprob, probs, nrhs, f_dev, x_dev, tol, max_it, stats, (cudaStream_t)stream);
+    if (rc != DCG_OK) return rc;
+    int worst = DCG_OK;
+    for (int k = 0; k < nprob * nrhs; ++k)
+      if (stats[k].status != DCG_OK && worst == DCG_OK) worst = stats[k].status;
+    return worst;
+  }
   // Problems are independent: a pool of host workers drives them on their own
   // non-blocking streams (each problem's right-hand sides in order), so the
   // GPU overlaps the latency-bound kernels of different problems. Work starts
@@ -494,6 +509,7 @@ int dcg_autotune(dcg_problem* p, const dcg_options* base, const double* f_dev, d
 
 void dcg_destroy(dcg_problem* p) {
   if (!p) return;
+  graph_free(p);
   mg_free(p);
   prof_flush(p);
   prof_clear_graph(p);
@@ -613,6 +629,7 @@ int dcg_profile_enable(dcg_problem* p, unsigned mask, void* stream) {
   }
   const bool rebuild = P.mask != mask;
   P.mask = mask;
+  graph_free(p);
   if (rebuild && p->is_setup) return mg_rebuild_graph(p);
   return DCG_OK;
 }

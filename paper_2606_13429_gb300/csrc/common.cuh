@@ -281,6 +281,16 @@ struct dcg_problem {
   double* fine_x64 = nullptr;
   dcg::Prof prof;
   dcg::MGState mg;
+  // solve captured into one CUDA graph (graph.cu): device state, the
+  // instantiated graph and the arguments it was captured for, and the
+  // kernels its loop bodies launch per iteration (top, pass, outer, cycle)
+  void* gstate = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const double* gkey_f = nullptr;
+  double* gkey_x = nullptr;
+  double gkey_tol = 0.0;
+  int gkey_maxit = 0;
+  long long gcounts[4] = {0, 0, 0, 0};
 };
 
 namespace dcg {
@@ -354,6 +364,22 @@ int vec_zero(double* dst, long long n, cudaStream_t s);
 
 // solver
 int solve_device(dcg_problem* p, const double* f, double* x, double tol, int max_it, dcg_stats* st, cudaStream_t s);
+// launch wrappers of the outer iteration shared with the captured solve;
+// stop: device flag that makes the direction kernels skip (may be null)
+int solver_update(dcg_problem* p, double* x, double* r, const double* d, const double* q, int use_dr,
+                  cudaStream_t s);
+int solver_direction(dcg_problem* p, double* d, const double* r, int fcg, cudaStream_t s, const int* stop);
+int solver_fcg_store(dcg_problem* p, cudaStream_t s);
+int solver_fcg_direction(dcg_problem* p, cudaStream_t s, const int* stop, int K, int finish_grid);
+int solver_reconstruct(dcg_problem* p, const double* xh, const double* z1, const double* zf, double* x,
+                       cudaStream_t s);
+int solver_axpy(dcg_problem* p, double* y, const double* x, cudaStream_t s);
+// the whole solve as one CUDA graph with device-side loop control (graph.cu)
+bool graph_solve_supported(const dcg_problem* p);
+int graph_solve(dcg_problem* p, const double* f, double* x, double tol, int max_it, dcg_stats* st, cudaStream_t s);
+int graph_solve_batched(int nprob, dcg_problem* const* probs, int nrhs, const double* const* f, double* const* x,
+                        double tol, int max_it, dcg_stats* stats, cudaStream_t s);
+void graph_free(dcg_problem* p);
 int read_scalars(dcg_problem* p, cudaStream_t s);
 
 // multigrid
@@ -365,6 +391,11 @@ int mg_cycles(dcg_problem* p, const double* g, double* z, int ncycles, cudaStrea
 int mg_solve(dcg_problem* p, const double* g, double* z, double tol, int nmax, int* ncyc, cudaStream_t s);
 std::vector<int> level_sizes(int n, int max_levels);  // mesh sizes n_J, n_J/2, ... (finest first)
 int mg_ras_step_hook(dcg_problem* p, int level, const double* f, double* z, cudaStream_t s);
+// pieces of Algorithm 3 for the graph-captured solve (graph.cu)
+int mg_graph_residual(dcg_problem* p, const double* g, const double* z, bool with_g, cudaStream_t s);
+int mg_graph_wcycle(dcg_problem* p, cudaStream_t s);
+int mg_graph_accumulate(dcg_problem* p, double* z, cudaStream_t s);
+bool mg_exact(const dcg_problem* p);
 int mg_coarse_hook(dcg_problem* p, const double* f, double* z, cudaStream_t s);
 
 }  // namespace dcg

@@ -1200,6 +1200,12 @@ __global__ void k_inner_residual(Stencil<double> st, const double* __restrict__ 
 }
 
 template <typename T>
+__global__ void k_fill_zero(T* __restrict__ z, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = (T)0;
+}
+
+template <typename T>
 __global__ void k_accumulate(double* __restrict__ z, const T* __restrict__ c, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     z[i] += (double)c[i];
@@ -1736,7 +1742,8 @@ int wcycle_t(dcg_problem* p, int k, cudaStream_t s, bool z_zero) {
   DCG_LAUNCH_CHECK();
   prof_end(p, prof, s, 2.0 * (ipow(3, D) * (double)L.nn + ipow(3, D) * (double)Lc.nn),
            sizeof(T) * (4.0 * L.nn + Lc.nn), g_capturing);
-  DCG_CUDA(cudaMemsetAsync(Lc.z, 0, sizeof(T) * Lc.nn, s));
+  k_fill_zero<T><<<grid_for(Lc.nn, 256, 8192), 256, 0, s>>>((T*)Lc.z, Lc.nn);  // a kernel: graph bodies take it
+  DCG_LAUNCH_CHECK();
   DCG_TRY((wcycle_t<T, D>(p, k - 1, s, true)));
   // Algorithm 4's second recursive call W_{k-1}(r_c, e1): on the coarsest
   // level W is the exact solve, which ignores the initial guess, so the second
@@ -2092,6 +2099,24 @@ int mg_solve(dcg_problem* p, const double* g, double* z, double tol, int nmax, i
   *ncyc = n;
   return DCG_OK;
 }
+
+// Pieces of Algorithm 3 for a solve captured into one CUDA graph (graph.cu):
+// the FP64 residual of the inner system into the cycle's input (||r||^2 to
+// S_TMP0 and, with with_g, ||g||^2 to S_TMP1), one W-cycle launched as
+// kernels on the capturing stream, and z += the cycle's correction.
+int mg_graph_residual(dcg_problem* p, const double* g, const double* z, bool with_g, cudaStream_t s) {
+  return p->mg.fp32 ? inner_residual<float>(p, g, z, s, with_g) : inner_residual<double>(p, g, z, s, with_g);
+}
+int mg_graph_wcycle(dcg_problem* p, cudaStream_t s) {
+  g_capturing = true;
+  const int st = p->mg.fp32 ? wcycle_dispatch<float>(p, s) : wcycle_dispatch<double>(p, s);
+  g_capturing = false;
+  return st;
+}
+int mg_graph_accumulate(dcg_problem* p, double* z, cudaStream_t s) {
+  return p->mg.fp32 ? accumulate<float>(p, z, s) : accumulate<double>(p, z, s);
+}
+bool mg_exact(const dcg_problem* p) { return exact_mode(p); }
 
 int mg_ras_step_hook(dcg_problem* p, int level, const double* f, double* z, cudaStream_t s) {
   if (level < 2 || level > (int)p->levels.size()) return DCG_ERR_INVALID_ARG;

@@ -57,8 +57,11 @@ __global__ void k_update(double* __restrict__ x, double* __restrict__ r, const d
 // FR:   d = r + (rr_new / rr) d
 // FCG1: d = r - (rq / dq) d
 // then d.r -> S_DR and S_RR <- rr_new
+// stop (device flag, may be null): the loop of a captured solve has ended and
+// the next direction is not needed (uniform early exit of every CTA)
 __global__ void k_direction(double* __restrict__ d, const double* __restrict__ r, long long n, double* __restrict__ sc,
-                            int fcg, Reduce red) {
+                            int fcg, Reduce red, const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const double rrn = sc[S_RRN];  // r.r of the new residual (written by k_update)
   const double beta = fcg ? -(sc[S_RQ] / sc[S_DQ]) : rrn / sc[S_RR];
   double part[1] = {0.0};
@@ -73,7 +76,10 @@ __global__ void k_direction(double* __restrict__ d, const double* __restrict__ r
 }
 
 // after k_direction has read both: S_RR <- S_RRN
-__global__ void k_roll(double* sc) { sc[S_RR] = sc[S_RRN]; }
+__global__ void k_roll(double* sc, const int* __restrict__ stop) {
+  if (stop && *stop) return;
+  sc[S_RR] = sc[S_RRN];
+}
 
 // FCG with the truncation-restart rule of the remark after Table 4: the
 // direction d_i (i = number of directions stored so far, ndir[0]) is
@@ -110,8 +116,9 @@ constexpr int kMultiDot = 8;
 constexpr int kMultiDotGrid = 2 * 152;  // CTAs along the vector (partials per direction)
 __global__ void __launch_bounds__(kRedThreads) k_multi_dot(const double* __restrict__ r, const double* __restrict__ qdirs,
                                                             const int* __restrict__ ndir, int cap, long long n,
-                                                            double* __restrict__ part) {
+                                                            double* __restrict__ part, const int* __restrict__ stop) {
   __shared__ double smem[32 * kMultiDot];
+  if (stop && *stop) return;
   const int i = ndir[0];
   const int K = fcg_window(i, cap), first = i - K;
   const int j0 = blockIdx.y * kMultiDot;
@@ -137,8 +144,9 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_dot(const double* __restr
 
 // coef[j] = sum over CTAs of part[j][.] (one CTA per window entry)
 __global__ void k_multi_dot_finish(const double* __restrict__ part, int nbx, const int* __restrict__ ndir, int cap,
-                                   double* __restrict__ coef) {
+                                   double* __restrict__ coef, const int* __restrict__ stop) {
   __shared__ double smem[32];
+  if (stop && *stop) return;
   const int K = fcg_window(ndir[0], cap);
   const int j = blockIdx.x;
   if (j >= K) return;
@@ -151,7 +159,9 @@ __global__ void k_multi_dot_finish(const double* __restrict__ part, int nbx, con
 // d_i = r - sum_j (c_j / dq_{first+j}) d_{first+j}; (d_i, r) -> red
 __global__ void k_orth_direction(double* __restrict__ d, const double* __restrict__ r, const double* __restrict__ dirs,
                                  const double* __restrict__ coef, const double* __restrict__ dqs,
-                                 const int* __restrict__ ndir, int cap, long long n, Reduce red) {
+                                 const int* __restrict__ ndir, int cap, long long n, Reduce red,
+                                 const int* __restrict__ stop) {
+  if (stop && *stop) return;
   const int i = ndir[0];
   const int K = fcg_window(i, cap), first = i - K;
   double part[1] = {0.0};
@@ -299,19 +309,10 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged, 
     }
     if (fcginf) {
       // d_{i-1}, q_{i-1} and their product into the ring before the update
-      const int prof2 = prof_begin(p, PC_VEC, s);
-      k_store_dir<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.q, b.dirs, b.qdirs, b.ndir_dev, b.ndir_cap, N);
-      DCG_LAUNCH_CHECK();
-      k_store_dq<<<1, 1, 0, s>>>(b.dqs, p->scal, b.ndir_dev, b.ndir_cap);
-      DCG_LAUNCH_CHECK();
-      prof_end(p, prof2, s, 0.0, 32.0 * N);
+      DCG_TRY(solver_fcg_store(p, s));
       ++ndir;
     }
-    int prof = prof_begin(p, PC_VEC, s);
-    k_update<<<grid_n(N), kRedThreads, 0, s>>>(b.xh, b.r, b.d, b.q, N, p->scal, c.rule != R_FR,
-                                               make_reduce(p, S_RRN));
-    DCG_LAUNCH_CHECK();
-    prof_end(p, prof, s, 8.0 * N, 48.0 * N);
+    DCG_TRY(solver_update(p, b.xh, b.r, b.d, b.q, c.rule != R_FR, s));
     c.st->outer_its++;
     DCG_TRY(read_scalars(p, s));
     const double dq = p->scal_host[S_DQ];
@@ -346,34 +347,17 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged, 
       const int mi = std::max(1, ndir % (b.ndir_cap + 1));
       const int K = std::min(mi, ndir);
       if (K < ndir) c.st->fcg_truncated++;
-      const int gy = (K + 7) / 8;
-      const int prof2 = prof_begin(p, PC_VEC, s);
-      k_multi_dot<<<dim3(kMultiDotGrid, gy), kRedThreads, 0, s>>>(b.r, b.qdirs, b.ndir_dev, b.ndir_cap, N, b.part);
-      DCG_LAUNCH_CHECK();
-      k_multi_dot_finish<<<K, kRedThreads, 0, s>>>(b.part, kMultiDotGrid, b.ndir_dev, b.ndir_cap, b.coef);
-      DCG_LAUNCH_CHECK();
-      k_orth_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, b.dirs, b.coef, b.dqs, b.ndir_dev, b.ndir_cap,
-                                                          N, make_reduce(p, S_DR));
-      DCG_LAUNCH_CHECK();
-      prof_end(p, prof2, s, 4.0 * K * N, 8.0 * N * (2.0 * K + 2.0 + (double)gy));
+      DCG_TRY(solver_fcg_direction(p, s, nullptr, K, K));
     } else {
-      prof = prof_begin(p, PC_VEC, s);
-      k_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, N, p->scal, c.rule == R_FCG1, make_reduce(p, S_DR));
-      DCG_LAUNCH_CHECK();
-      prof_end(p, prof, s, 4.0 * N, 24.0 * N);
+      DCG_TRY(solver_direction(p, b.d, b.r, c.rule == R_FCG1, s, nullptr));
     }
-    k_roll<<<1, 1, 0, s>>>(p->scal);
-    DCG_LAUNCH_CHECK();
     rr = rrn;
   }
   // reconstruction x = xh - pi(A xh) + pi(f)
   DCG_TRY(pi_of_Ax(c, b.xh, b.zh, tc0, false));
   const int g = grid_n(N);
-  const double isd = 1.0 / std::sqrt((double)p->dim);
-  if (p->dim == 2) k_reconstruct<2><<<g, kRedThreads, 0, s>>>(b.xh, b.zh, b.zf, x, p->n_nodes, isd);
-  else k_reconstruct<3><<<g, kRedThreads, 0, s>>>(b.xh, b.zh, b.zf, x, p->n_nodes, isd);
-  DCG_LAUNCH_CHECK();
-  return DCG_OK;
+  (void)g;
+  return solver_reconstruct(p, b.xh, b.zh, b.zf, x, s);
 }
 
 int plain_cg(Ctx& c, const double* f, double* x) {
@@ -388,10 +372,7 @@ int plain_cg(Ctx& c, const double* f, double* x) {
   bool conv = std::sqrt(rr) <= c.eps;
   while (!conv && c.st->outer_its < c.max_it) {
     DCG_TRY(spmv_dot(p, b.d, b.q, b.d, S_DQ, s));
-    int prof = prof_begin(p, PC_VEC, s);
-    k_update<<<grid_n(N), kRedThreads, 0, s>>>(x, b.r, b.d, b.q, N, p->scal, 0, make_reduce(p, S_RRN));
-    DCG_LAUNCH_CHECK();
-    prof_end(p, prof, s, 8.0 * N, 48.0 * N);
+    DCG_TRY(solver_update(p, x, b.r, b.d, b.q, 0, s));
     c.st->outer_its++;
     bool check = (c.st->outer_its % std::max(1, p->opts.check_every)) == 0;
     if (check) {
@@ -407,17 +388,84 @@ int plain_cg(Ctx& c, const double* f, double* x) {
         break;
       }
     }
-    prof = prof_begin(p, PC_VEC, s);
-    k_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, N, p->scal, 0, make_reduce(p, S_DR));
-    DCG_LAUNCH_CHECK();
-    prof_end(p, prof, s, 4.0 * N, 24.0 * N);
-    k_roll<<<1, 1, 0, s>>>(p->scal);
-    DCG_LAUNCH_CHECK();
+    DCG_TRY(solver_direction(p, b.d, b.r, 0, s, nullptr));
   }
   return DCG_OK;
 }
 
 }  // namespace
+
+// Launch wrappers shared by the host-driven loop below and the captured
+// solve of graph.cu.
+int solver_update(dcg_problem* p, double* x, double* r, const double* d, const double* q, int use_dr,
+                  cudaStream_t s) {
+  const long long N = p->N;
+  const int prof = prof_begin(p, PC_VEC, s);
+  k_update<<<grid_n(N), kRedThreads, 0, s>>>(x, r, d, q, N, p->scal, use_dr, make_reduce(p, S_RRN));
+  DCG_LAUNCH_CHECK();
+  prof_end(p, prof, s, 8.0 * N, 48.0 * N);
+  return DCG_OK;
+}
+
+int solver_direction(dcg_problem* p, double* d, const double* r, int fcg, cudaStream_t s, const int* stop) {
+  const long long N = p->N;
+  const int prof = prof_begin(p, PC_VEC, s);
+  k_direction<<<grid_n(N), kRedThreads, 0, s>>>(d, r, N, p->scal, fcg, make_reduce(p, S_DR), stop);
+  DCG_LAUNCH_CHECK();
+  prof_end(p, prof, s, 4.0 * N, 24.0 * N);
+  k_roll<<<1, 1, 0, s>>>(p->scal, stop);
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
+
+int solver_fcg_store(dcg_problem* p, cudaStream_t s) {
+  SolverBuffers& b = p->sb;
+  const long long N = p->N;
+  const int prof = prof_begin(p, PC_VEC, s);
+  k_store_dir<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.q, b.dirs, b.qdirs, b.ndir_dev, b.ndir_cap, N);
+  DCG_LAUNCH_CHECK();
+  k_store_dq<<<1, 1, 0, s>>>(b.dqs, p->scal, b.ndir_dev, b.ndir_cap);
+  DCG_LAUNCH_CHECK();
+  prof_end(p, prof, s, 0.0, 32.0 * N);
+  return DCG_OK;
+}
+
+// K: launch shape for the window (the kernels read the actual window from the
+// device counter and skip entries beyond it; a captured solve passes the ring
+// size)
+int solver_fcg_direction(dcg_problem* p, cudaStream_t s, const int* stop, int K, int finish_grid) {
+  SolverBuffers& b = p->sb;
+  const long long N = p->N;
+  const int gy = (K + kMultiDot - 1) / kMultiDot;
+  const int prof = prof_begin(p, PC_VEC, s);
+  k_multi_dot<<<dim3(kMultiDotGrid, gy), kRedThreads, 0, s>>>(b.r, b.qdirs, b.ndir_dev, b.ndir_cap, N, b.part, stop);
+  DCG_LAUNCH_CHECK();
+  k_multi_dot_finish<<<finish_grid, kRedThreads, 0, s>>>(b.part, kMultiDotGrid, b.ndir_dev, b.ndir_cap, b.coef, stop);
+  DCG_LAUNCH_CHECK();
+  k_orth_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, b.dirs, b.coef, b.dqs, b.ndir_dev, b.ndir_cap, N,
+                                                      make_reduce(p, S_DR), stop);
+  DCG_LAUNCH_CHECK();
+  prof_end(p, prof, s, 4.0 * K * N, 8.0 * N * (2.0 * K + 2.0 + (double)gy));
+  k_roll<<<1, 1, 0, s>>>(p->scal, stop);
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
+
+int solver_reconstruct(dcg_problem* p, const double* xh, const double* z1, const double* zf, double* x,
+                       cudaStream_t s) {
+  const int g = grid_n(p->N);
+  const double isd = 1.0 / std::sqrt((double)p->dim);
+  if (p->dim == 2) k_reconstruct<2><<<g, kRedThreads, 0, s>>>(xh, z1, zf, x, p->n_nodes, isd);
+  else k_reconstruct<3><<<g, kRedThreads, 0, s>>>(xh, z1, zf, x, p->n_nodes, isd);
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
+
+int solver_axpy(dcg_problem* p, double* y, const double* x, cudaStream_t s) {
+  k_axpy<<<grid_n(p->N), kRedThreads, 0, s>>>(y, x, p->N);
+  DCG_LAUNCH_CHECK();
+  return DCG_OK;
+}
 
 int read_scalars(dcg_problem* p, cudaStream_t s) {
   DCG_CUDA(cudaMemcpyAsync(p->scal_host, p->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
@@ -432,6 +480,7 @@ int read_scalars(dcg_problem* p, cudaStream_t s) {
 
 int solve_device(dcg_problem* p, const double* f, double* x, double tol, int max_it, dcg_stats* st,
                  cudaStream_t s) {
+  if (graph_solve_supported(p)) return graph_solve(p, f, x, tol, max_it, st, s);
   auto t0 = std::chrono::steady_clock::now();
   *st = dcg_stats{};
   st->status = DCG_OK;
@@ -482,8 +531,7 @@ int solve_device(dcg_problem* p, const double* f, double* x, double tol, int max
       st->restarts++;
       bool conv = false;
       DCG_TRY(fdcg_pass(c, b.u, b.e, false, &conv, &stalled));
-      k_axpy<<<grid_n(N), kRedThreads, 0, s>>>(x, b.e, N);
-      DCG_LAUNCH_CHECK();
+      DCG_TRY(solver_axpy(p, x, b.e, s));
       DCG_TRY(spmv_residual(p, f, x, b.u, S_TMP0, s));
       DCG_TRY(read_scalars(p, s));
       st->true_relres = std::sqrt(p->scal_host[S_TMP0]) / c.fnorm;

@@ -43,7 +43,7 @@ class dcg_options(C.Structure):
                 ("recurrence", C.c_int), ("precision", C.c_int), ("ras_inverse", C.c_int),
                 ("ras_weights", C.c_int), ("deflate", C.c_int), ("max_restarts", C.c_int),
                 ("fcg_max_dirs", C.c_int), ("check_every", C.c_int),
-                ("stall_window", C.c_int)]
+                ("stall_window", C.c_int), ("device_loop", C.c_int)]
 
 
 class dcg_stats(C.Structure):
