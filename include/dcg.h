@@ -274,6 +274,57 @@ int dcg_ras_step(dcg_problem* p, int level, const double* f_dev, double* z_dev, 
 /* Exact coarsest-level solve z = Z_1^-1 f (FP64 arrays of level-1 size). */
 int dcg_coarse_solve(dcg_problem* p, const double* f_dev, double* z_dev, void* stream);
 
+/* ---- time stepping and reconstruction (Section 2.3; Section 5.2) ------- */
+#define DCG_IMPLICIT_EULER  0  /* theta-method with theta = 1: alpha = dt */
+#define DCG_CRANK_NICOLSON  1  /* theta = 1/2: alpha = dt / 2 */
+#define DCG_BDF2            2  /* alpha = 2 dt / 3; the first step takes sigma^-1 = sigma^0 */
+
+/* alpha(dt) of a scheme (Eq. weak_IE: a step solves (M + alpha A) sigma^n =
+ * F*_n, i.e. this library's A_alpha = M_dev / alpha + K_div): assemble the
+ * problem with dt = dcg_scheme_alpha(scheme, dt) to step with `dt`.
+ * Returns -1 for an unknown scheme. */
+double dcg_scheme_alpha(int scheme, double dt);
+
+/* y = K_div x, the divergence form alone (N doubles in and out, device), by
+ * the constant 3^d stencil of the uniform Q1 mesh (Section 3.2.1, a_ij). */
+int dcg_apply_div(const dcg_problem* p, const double* x, double* y, void* stream);
+
+/* Right-hand side b^n of one step for a problem assembled with alpha =
+ * dcg_scheme_alpha(scheme, dt), from the previous steps s1 = sigma^{n-1},
+ * s2 = sigma^{n-2} (BDF2 only; NULL = s1) and the load vectors F1 = F^n,
+ * F0 = F^{n-1} (Crank-Nicolson only) of the forcing:
+ *   implicit Euler  b = (M_dev/alpha) s1 + F1
+ *   Crank-Nicolson  b = (M_dev/alpha - K_div) s1 + F1 + F0
+ *   BDF2            b = (M_dev/alpha)(4/3 s1 - 1/3 s2) + F1
+ * (M_dev/alpha) w is formed as A_alpha w - K_div w. Device arrays of N
+ * doubles; a scratch of 3 N doubles is allocated on `stream` for the call. */
+int dcg_time_rhs(dcg_problem* p, int scheme, const double* s1, const double* s2, const double* F1,
+                 const double* F0, double* rhs, void* stream);
+
+/* Pressure p = -(1/d) tr(sigma) at every interior node (Section 5.2):
+ * sigma N doubles in, pres n_nodes doubles out (device). */
+int dcg_pressure(const dcg_problem* p, const double* sigma, double* pres, void* stream);
+
+/* (div sigma)_k = sum_p d_p sigma_kp at every element centre, where it is
+ * exact for the Q1 fields (the mean over the element's edges along p of the
+ * difference quotients); elements lexicographic (x fastest), d values per
+ * element: n^d * d doubles out (device). */
+int dcg_divergence(const dcg_problem* p, const double* sigma, double* div_elem, void* stream);
+
+/* nsteps steps of `scheme` with step dt (the problem assembled with alpha =
+ * dcg_scheme_alpha(scheme, dt) and set up): F[0..nsteps] the load vectors
+ * F^n of the forcing at t_n, sigma0 the initial stress, sigma_out[0..nsteps-1]
+ * receive sigma^1..sigma^nsteps (each step solves to tol from the previous
+ * step as initial guess; stats[k], if given, its statistics). u_elem (may be
+ * NULL): element-centre velocity u = u_0 + int div(sigma) dt (Section 5.2),
+ * n^d * d doubles in (u_0) and out, integrated by the scheme's own rule
+ * (right endpoint for implicit Euler and BDF2, trapezoid for Crank-Nicolson).
+ * Returns the first non-OK step status (later steps are not run). Scratch of
+ * 4 N + 2 d n^d doubles is allocated for the call. */
+int dcg_time_integrate(dcg_problem* p, int scheme, double dt, int nsteps, const double* sigma0,
+                       const double* const* F, double* const* sigma_out, double* u_elem, double tol, int max_it,
+                       dcg_stats* stats, void* stream);
+
 /* ---- timing of kernel classes (CUDA events, off by default) ----------- */
 #define DCG_PROF_SPMV        0  /* operator products (fused BSR variants, matrix-free) */
 #define DCG_PROF_VEC         1  /* vector updates and reductions */

@@ -18,10 +18,13 @@ fusion or reordering beyond what the paper's definitions state:
 * ``solvers`` -- plain CG and the flexible deflated CG (Section 4.1,
                  Eqs. x_defl / defl_sys / inner / fixed_tol / tol, Algorithms 1
                  and 2; truncation rule of the FCG remark in Section 5.1).
+* ``timestep`` -- implicit Euler, Crank-Nicolson and BDF2 steps of Eq.
+                 weak_IE (Section 2.3) and the pressure / velocity
+                 reconstruction of Section 5.2.
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 against closed forms, textbook identities, the matrices the paper prints for
 d = 2 and d = 3, brute force on tiny meshes and dense direct solves. None is
 "parity unpinned".
 """
-from . import fem, mg, solvers  # noqa: F401
+from . import fem, mg, solvers, timestep  # noqa: F401

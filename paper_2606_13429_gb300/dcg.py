@@ -30,6 +30,7 @@ DCG_FCG1, DCG_FR, DCG_FCG_INF = 0, 1, 2
 DCG_FP64, DCG_MIXED = 0, 1
 DCG_INV_FP32, DCG_INV_BF16 = 0, 1
 DCG_RAS_MULTIPLICITY, DCG_RAS_RESTRICTED = 0, 1
+DCG_IMPLICIT_EULER, DCG_CRANK_NICOLSON, DCG_BDF2 = 0, 1, 2
 PROF_CLASSES = ["spmv", "vec", "ras_solve", "ras_update", "transfer", "coarse", "inner_res"]
 
 
@@ -100,6 +101,13 @@ def load(path: str = LIB_PATH):
         "dcg_profile_read": (I, [P, I, C.POINTER(D), C.POINTER(LL), C.POINTER(D), C.POINTER(D), VP]),
         "dcg_kernel_launches": (LL, []),
         "dcg_measure_fma_rate": (I, [I, C.POINTER(D), VP]),
+        "dcg_scheme_alpha": (D, [I, D]),
+        "dcg_apply_div": (I, [P, VP, VP, VP]),
+        "dcg_time_rhs": (I, [P, I, VP, VP, VP, VP, VP, VP]),
+        "dcg_pressure": (I, [P, VP, VP, VP]),
+        "dcg_divergence": (I, [P, VP, VP, VP]),
+        "dcg_time_integrate": (I, [P, I, D, I, VP, C.POINTER(VP), C.POINTER(VP), VP, D, I, C.POINTER(dcg_stats),
+                                   VP]),
         "dcg_selftest_bounded_wait": (I, [C.c_uint, C.POINTER(I), VP]),
         "dcg_coarse_solve_static": (I, [P, VP, VP, VP]),
         "dcg_autotune": (I, [P, C.POINTER(dcg_options), VP, D, I, C.POINTER(dcg_options), C.POINTER(D), VP]),
@@ -379,6 +387,50 @@ def dcg_selftest_bounded_wait(max_polls, stream=None) -> bool:
     g = C.c_int()
     _check(load().dcg_selftest_bounded_wait(max_polls, C.byref(g), _stream(stream)), "dcg_selftest_bounded_wait")
     return bool(g.value)
+
+
+def dcg_scheme_alpha(scheme, dt) -> float:
+    return float(load().dcg_scheme_alpha(scheme, dt))
+
+
+def dcg_apply_div(prob: Problem, x, y, stream=None):
+    _check(load().dcg_apply_div(prob.ptr, _dptr(x, prob.N, "x"), _dptr(y, prob.N, "y"), _stream(stream)),
+           "dcg_apply_div")
+
+
+def dcg_time_rhs(prob: Problem, scheme, s1, F1, rhs, s2=None, F0=None, stream=None):
+    _check(load().dcg_time_rhs(prob.ptr, scheme, _dptr(s1, prob.N, "s1"),
+                               _dptr(s2, prob.N, "s2") if s2 is not None else None, _dptr(F1, prob.N, "F1"),
+                               _dptr(F0, prob.N, "F0") if F0 is not None else None, _dptr(rhs, prob.N, "rhs"),
+                               _stream(stream)), "dcg_time_rhs")
+
+
+def dcg_pressure(prob: Problem, sigma, pres, stream=None):
+    _check(load().dcg_pressure(prob.ptr, _dptr(sigma, prob.N, "sigma"), _dptr(pres, prob.n_nodes, "pres"),
+                               _stream(stream)), "dcg_pressure")
+
+
+def dcg_divergence(prob: Problem, sigma, div_elem, stream=None):
+    ne = prob.n ** prob.dim
+    _check(load().dcg_divergence(prob.ptr, _dptr(sigma, prob.N, "sigma"), _dptr(div_elem, ne * prob.dim, "div"),
+                                 _stream(stream)), "dcg_divergence")
+
+
+def dcg_time_integrate(prob: Problem, scheme, dt, sigma0, loads, sigma_out, u_elem=None, tol=1e-8, max_it=100000,
+                       stream=None):
+    """loads: nsteps+1 device arrays F^0..F^nsteps; sigma_out: nsteps arrays."""
+    nsteps = len(sigma_out)
+    if len(loads) != nsteps + 1:
+        raise ValueError("need nsteps + 1 load vectors")
+    Fp = (C.c_void_p * (nsteps + 1))(*[_dptr(f, prob.N, "F").value for f in loads])
+    Sp = (C.c_void_p * nsteps)(*[_dptr(x, prob.N, "sigma_out").value for x in sigma_out])
+    stats = (dcg_stats * nsteps)()
+    ne = prob.n ** prob.dim
+    code = load().dcg_time_integrate(prob.ptr, scheme, dt, nsteps, _dptr(sigma0, prob.N, "sigma0"), Fp, Sp,
+                                     _dptr(u_elem, ne * prob.dim, "u") if u_elem is not None else None, tol, max_it,
+                                     stats, _stream(stream))
+    _check(code, "dcg_time_integrate", ok=(DCG_OK, DCG_ERR_NOT_CONVERGED, DCG_ERR_BREAKDOWN))
+    return code, [st.as_dict() for st in stats]
 
 
 def dcg_kernel_launches() -> int:
