@@ -72,6 +72,10 @@ extern "C" {
 #define DCG_FCG_INF  2  /* FCG of Algorithm 1 with directions stored; untruncated while a
                            pass has at most fcg_max_dirs iterations, then the
                            truncation-restart rule of the remark after Table 4 */
+#define DCG_GMRES    3  /* GMRES on the deflated system (remarks in Sections 4.3 and 5.1):
+                           Arnoldi with classical Gram-Schmidt applied twice, restart
+                           length fcg_max_dirs, inner tolerance of Eq. tol from the
+                           least-squares residual norm; host-driven loop */
 
 #define DCG_FP64   0  /* everything in FP64 */
 #define DCG_MIXED  1  /* W-cycle (stencils, transfers, RAS) in FP32; outer CG FP64 */
@@ -102,7 +106,7 @@ typedef struct {
   int inner_rule;    /* DCG_INNER_* [FIXED] */
   double c;          /* c_F or c_A [0.01] */
   int inner_nmax;    /* W-cycle cap per inner solve, Algorithm 3 n_max [100] */
-  int recurrence;    /* DCG_FCG1 / DCG_FR / DCG_FCG_INF [FCG1] */
+  int recurrence;    /* DCG_FCG1 / DCG_FR / DCG_FCG_INF / DCG_GMRES [FCG1] */
   int precision;     /* DCG_FP64 / DCG_MIXED [FP64] */
   int ras_inverse;   /* DCG_INV_* (mixed only) [FP32] */
   int ras_weights;   /* DCG_RAS_* [MULTIPLICITY] */
@@ -114,7 +118,9 @@ typedef struct {
                         recent directions, so a pass of at most m_max
                         iterations is the untruncated FCG(inf). Directions
                         d and M_D d are kept in 2 * m_max device vectors of N
-                        doubles. 0 = min(256, the count that fits 8 GiB) [0] */
+                        doubles. DCG_GMRES: the restart length (m_max + 1
+                        basis vectors). 0 = min(256, the count that fits
+                        8 GiB) [0] */
   int check_every;   /* plain CG only: iterations between host convergence
                         reads (deflated CG reads every iteration) [1] */
   int stall_window;  /* deflated CG: a pass whose recursive residual has not

@@ -29,6 +29,13 @@ Recurrences (Algorithm 1; truncation rule of the FCG remark):
   m_i most recent directions d_{i-m_i}, ..., d_{i-1} only. m_max = 0 gives
   FCG(1); m_max at least the iteration count gives the untruncated method.
 * "fr": classical CG coefficients, alpha = (r,r)/(d,q), beta = (r',r')/(r,r).
+* "gmres": GMRES on the deflated system (the alternative outer solver of the
+  remarks in Sections 4.3 and 5.1): Arnoldi with modified Gram-Schmidt on
+  the vectors M_D(v_j, tau_c) the inexact operator returns, each v_j's inner
+  tolerance from Eq. tol with ||r_j|| the least-squares residual norm;
+  Givens rotations give that norm after every step, which is the stopping
+  test. m_max = None: full GMRES; an integer: restarted GMRES(m_max), each
+  restart from the recursive residual f_D - M_D x_hat.
 
 Reading (not in the paper): after reconstruction the true residual
 ||f - A x|| / ||f|| is computed in FP64; if it is above tol, the same FDCG is
@@ -106,8 +113,8 @@ class FDCGOptions:
     inner_rule: str = "fixed"      # "fixed" | "adaptive" | "exact"
     c: float = 0.01                # c_F or c_A
     inner_nmax: int = 100
-    recurrence: str = "fcg1"       # "fcg1" | "fr" | "fcg_inf"
-    m_max: int | None = None       # fcg_inf: truncation-restart parameter (None = untruncated)
+    recurrence: str = "fcg1"       # "fcg1" | "fr" | "fcg_inf" | "gmres"
+    m_max: int | None = None       # fcg_inf: truncation-restart parameter; gmres: restart length (None = none)
     max_restarts: int = 3
     stall_window: int = 0          # restart a pass whose residual stopped falling; 0 = off
 
@@ -219,6 +226,74 @@ class FDCG:
         x = xh - self.pi(A @ xh, tc0, st) + pi_f
         return x, conv, stalled
 
+    # GMRES pass ------------------------------------------------------------
+    def _pass_gmres(self, f, x0, eps, tol, max_it, st: SolveStats):
+        A, o = self.A, self.opts
+        tc0 = o.c * tol
+        pi_f = self.pi(f, tc0, st)
+        f_D = f - A @ pi_f
+        xh = np.zeros_like(f) if x0 is None else x0.copy()
+        r = f_D if x0 is None else f_D - self.M_D(xh, tc0, st)
+        conv = False
+        first = True
+        while not conv and st.outer_its < max_it:
+            beta = np.linalg.norm(r)
+            if first:
+                st.res0.append(beta)
+                first = False
+            if beta <= eps:
+                conv = True
+                break
+            m = o.m_max if o.m_max is not None else max_it
+            V = [r / beta]
+            Hc = []        # columns of the rotated Hessenberg matrix (upper triangular R)
+            cs, sn = [], []
+            g = [beta]
+            j = 0
+            while j < m and st.outer_its < max_it:
+                tc = self._inner_tol(abs(g[j]), eps, tol)
+                st.inner_tols.append(tc)
+                w = self.M_D(V[j], tc, st)
+                h = np.zeros(j + 2)
+                for i in range(j + 1):
+                    h[i] = V[i] @ w
+                    w = w - h[i] * V[i]
+                h[j + 1] = np.linalg.norm(w)
+                for i in range(j):  # previous rotations on the new column
+                    a, b = h[i], h[i + 1]
+                    h[i], h[i + 1] = cs[i] * a + sn[i] * b, -sn[i] * a + cs[i] * b
+                den = np.hypot(h[j], h[j + 1])
+                if den == 0.0:
+                    st.breakdown = True
+                    break
+                cs.append(h[j] / den)
+                sn.append(h[j + 1] / den)
+                h[j], h[j + 1] = den, 0.0
+                Hc.append(h[: j + 1])
+                g.append(-sn[j] * g[j])
+                g[j] = cs[j] * g[j]
+                st.outer_its += 1
+                st.history.append(abs(g[j + 1]))
+                nrm = np.linalg.norm(w)
+                if nrm > 0.0:
+                    V.append(w / nrm)
+                j += 1
+                if abs(g[j]) <= eps or nrm == 0.0:
+                    conv = True
+                    break
+            if j > 0:
+                R = np.zeros((j, j))
+                for c, col in enumerate(Hc[:j]):
+                    R[: c + 1, c] = col
+                y = np.linalg.solve(R, np.array(g[:j]))
+                for i in range(j):
+                    xh = xh + y[i] * V[i]
+            if st.breakdown or conv:
+                break
+            r = f_D - self.M_D(xh, tc0, st)  # restart from the recursive residual
+        x = xh - self.pi(A @ xh, tc0, st) + pi_f
+        return x, conv, False
+
     def solve(self, f: np.ndarray, tol: float = 1e-8, max_it: int = 100000, x0=None):
         st = SolveStats()
         fn = np.linalg.norm(f)
@@ -226,7 +301,8 @@ class FDCG:
             st.converged, st.true_relres = True, 0.0
             return np.zeros_like(f), st
         eps = tol * fn
-        x, conv, stalled = self._pass(f, x0, eps, tol, max_it, st)
+        run = self._pass_gmres if self.opts.recurrence == "gmres" else self._pass
+        x, conv, stalled = run(f, x0, eps, tol, max_it, st)
         res = f - self.A @ x
         st.true_relres = np.linalg.norm(res) / fn
         claimed = 0  # restarts after passes that reported convergence
@@ -235,7 +311,7 @@ class FDCG:
             if not stalled:
                 claimed += 1
             st.restarts += 1
-            e, conv, stalled = self._pass(res, None, eps, tol, max_it, st)
+            e, conv, stalled = run(res, None, eps, tol, max_it, st)
             x = x + e
             res = f - self.A @ x
             st.true_relres = np.linalg.norm(res) / fn

@@ -37,7 +37,7 @@ int check_options(const dcg_options* o, int dim) {
   if (!o) return DCG_ERR_INVALID_ARG;
   bool ok = o->max_levels >= 1 && o->patch >= 1 && o->overlap >= 0 && 2 * o->overlap <= o->patch && o->m1 >= 0 &&
             o->m2 >= 0 && (o->inner_rule >= 0 && o->inner_rule <= 2) && o->c > 0 && o->inner_nmax >= 1 &&
-            (o->recurrence >= 0 && o->recurrence <= 2) && (o->precision == DCG_FP64 || o->precision == DCG_MIXED) &&
+            (o->recurrence >= 0 && o->recurrence <= 3) && (o->precision == DCG_FP64 || o->precision == DCG_MIXED) &&
             (o->ras_inverse == DCG_INV_FP32 || o->ras_inverse == DCG_INV_BF16) &&
             (o->ras_weights == 0 || o->ras_weights == 1) && (o->deflate == 0 || o->deflate == 1) &&
             o->max_restarts >= 0 && o->fcg_max_dirs >= 0 && o->check_every >= 1 && o->stall_window >= 0 &&
@@ -274,7 +274,8 @@ int dcg_setup(dcg_problem* p, const dcg_options* opts, void* stream) {
     DCG_TRY(alloc_vec(&b.g, nn));
     DCG_TRY(alloc_vec(&b.zh, nn));
     DCG_TRY(alloc_vec(&b.zf, nn));
-    if (opts->recurrence == DCG_FCG_INF) {
+    if (opts->recurrence == DCG_FCG_INF || opts->recurrence == DCG_GMRES) {
+      const bool gm = opts->recurrence == DCG_GMRES;
       long long cap = opts->fcg_max_dirs;
       if (cap <= 0) {
         long long budget = (8LL << 30) / (16LL * N);
@@ -282,8 +283,10 @@ int dcg_setup(dcg_problem* p, const dcg_options* opts, void* stream) {
         if (cap < 1) cap = 1;
       }
       b.ndir_cap = (int)cap;
-      DCG_TRY(alloc_vec(&b.dirs, cap * N));
-      DCG_TRY(alloc_vec(&b.qdirs, cap * N));
+      // FCG: directions d_k and q_k = M_D d_k; GMRES: the Arnoldi basis
+      // (m + 1 vectors)
+      DCG_TRY(alloc_vec(&b.dirs, (gm ? cap + 1 : cap) * N));
+      DCG_TRY(alloc_vec(&b.qdirs, gm ? 1 : cap * N));
       DCG_TRY(alloc_vec(&b.dqs, cap));
       DCG_TRY(alloc_vec(&b.coef, cap));
       DCG_TRY(alloc_vec(&b.part, cap * 2 * 152));

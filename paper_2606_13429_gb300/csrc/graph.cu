@@ -420,7 +420,7 @@ int capture_graph(Fn build, cudaGraphExec_t* exec) {
 
 bool graph_solve_supported(const dcg_problem* p) {
   return p->opts.device_loop && p->opts.deflate && !mg_exact(p) && !p->matrix_free && p->prof.mask == 0 &&
-         p->sb.w != nullptr;
+         p->sb.w != nullptr && p->opts.recurrence != DCG_GMRES;
 }
 
 void graph_free(dcg_problem* p) {

@@ -25,13 +25,15 @@
 // and one host read of ||r|| for the stopping test.
 #include "common.cuh"
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <vector>
 
 namespace dcg {
 namespace {
 
-enum Rule { R_CG = 0, R_FCG1 = 1, R_FR = 2, R_FCGINF = 3 };
+enum Rule { R_CG = 0, R_FCG1 = 1, R_FR = 2, R_FCGINF = 3, R_GMRES = 4 };
 
 // x += a d; r -= a q; reduces (r.r, r.q) into (S_RRN, S_RQ);
 // a = (FCG ? d.r : r.r) / d.q, zero when d.q <= 0 (breakdown: the host stops).
@@ -176,6 +178,69 @@ __global__ void k_orth_direction(double* __restrict__ d, const double* __restric
     part[0] = fma(dt, rt, part[0]);
   }
   grid_reduce<1>(part, red);
+}
+
+// GMRES (the outer solver of the remarks in Sections 4.3 and 5.1): Arnoldi
+// with classical Gram-Schmidt applied twice against the basis V (K
+// contiguous vectors of n). h[i] = (V_i, w) per group of kMultiDot vectors
+// (blockIdx.y), per-CTA partial sums finished in block order.
+__global__ void __launch_bounds__(kRedThreads) k_gs_dots(const double* __restrict__ w, const double* __restrict__ V,
+                                                          int K, long long n, double* __restrict__ part) {
+  __shared__ double smem[32 * kMultiDot];
+  const int j0 = blockIdx.y * kMultiDot;
+  const double* vj[kMultiDot];
+#pragma unroll
+  for (int j = 0; j < kMultiDot; ++j) vj[j] = V + (size_t)min(j0 + j, K - 1) * n;
+  double acc[kMultiDot];
+#pragma unroll
+  for (int j = 0; j < kMultiDot; ++j) acc[j] = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double wt = w[t];
+#pragma unroll
+    for (int j = 0; j < kMultiDot; ++j) acc[j] = fma(wt, __ldg(vj[j] + t), acc[j]);
+  }
+  block_sum<kMultiDot>(acc, smem);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < kMultiDot; ++j)
+      if (j0 + j < K) part[(size_t)(j0 + j) * gridDim.x + blockIdx.x] = acc[j];
+  }
+}
+
+__global__ void k_gs_finish(const double* __restrict__ part, int nbx, double* __restrict__ h) {
+  __shared__ double smem[32];
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < nbx; b += blockDim.x) v[0] += part[(size_t)blockIdx.x * nbx + b];
+  block_sum<1>(v, smem);
+  if (threadIdx.x == 0) h[blockIdx.x] = v[0];
+}
+
+// w -= sum_i h_i V_i, and ||w||^2 -> red
+__global__ void k_gs_update(double* __restrict__ w, const double* __restrict__ V, const double* __restrict__ h, int K,
+                            long long n, Reduce red) {
+  double part[1] = {0.0};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double wt = w[t];
+    for (int i = 0; i < K; ++i) wt = fma(-h[i], V[(size_t)i * n + t], wt);
+    w[t] = wt;
+    part[0] = fma(wt, wt, part[0]);
+  }
+  grid_reduce<1>(part, red);
+}
+
+__global__ void k_scale_to(double* __restrict__ y, const double* __restrict__ x, double a, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+// x += sum_i y_i V_i
+__global__ void k_multi_axpy(double* __restrict__ x, const double* __restrict__ V, const double* __restrict__ y, int K,
+                             long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double v = x[t];
+    for (int i = 0; i < K; ++i) v = fma(y[i], V[(size_t)i * n + t], v);
+    x[t] = v;
+  }
 }
 
 // x = xh - V (z1 - zf) (Eq. x_defl with pi(A xh) = V z1, pi(f) = V zf)
@@ -360,6 +425,148 @@ int fdcg_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged, 
   return solver_reconstruct(p, b.xh, b.zh, b.zf, x, s);
 }
 
+// q = M_D v = A (v - pi(A v)) with the inner tolerance tc, into b.q (the
+// assembled operator: t = A v with g = V^T t, q = t - K_div V zh)
+int apply_md(Ctx& c, const double* v, double tc, bool in_iter) {
+  dcg_problem* p = c.p;
+  SolverBuffers& b = p->sb;
+  if (b.w) {
+    DCG_TRY(spmv_y_vt(p, v, b.w, b.g, S_GG, c.s));
+    DCG_TRY(inner_solve(c, b.zh, tc, in_iter));
+    DCG_TRY(q_from_t(p, b.w, b.zh, v, b.q, S_DQ, c.s));
+  } else {
+    DCG_TRY(pi_of_Ax(c, v, b.zh, tc, in_iter));
+    DCG_TRY(spmv_defl(p, v, b.zh, b.q, S_DQ, c.s, in_iter && mf_lowp(p)));
+  }
+  return DCG_OK;
+}
+
+// One pass of GMRES on the deflated system (restart length m = ndir_cap):
+// Arnoldi on the vectors M_D(v_j, tau_c) returns, classical Gram-Schmidt
+// twice, Givens rotations on the host give the residual norm after every
+// step (the stopping test, and ||r_j|| of Eq. tol); a restart begins from
+// the recursive residual f_D - M_D x_hat. Then the reconstruction of
+// Eq. x_defl, as in the FCG pass.
+int gmres_pass(Ctx& c, const double* f, double* x, bool use_x0, bool* converged) {
+  dcg_problem* p = c.p;
+  SolverBuffers& b = p->sb;
+  cudaStream_t s = c.s;
+  const long long N = p->N;
+  const double tc0 = p->opts.c * c.tol;
+  const int m = b.ndir_cap;
+  double* V = b.dirs;  // (m + 1) vectors of N
+  *converged = false;
+  DCG_TRY(vec_extract(p, f, b.g, S_GG, s));
+  DCG_TRY(vec_zero(b.zf, p->n_nodes, s));
+  {
+    int n = 0;
+    DCG_TRY(mg_solve(p, b.g, b.zf, tc0, p->opts.inner_nmax, &n, s));
+    c.st->total_mg_cycles += n;
+  }
+  DCG_TRY(spmv_f_minus_avz(p, f, b.zf, b.r, S_RR, s));
+  if (use_x0) {
+    DCG_TRY(vec_copy(b.xh, x, N, s));
+    DCG_TRY(apply_md(c, b.xh, tc0, false));
+    k_sub<<<grid_n(N), kRedThreads, 0, s>>>(b.r, b.q, N);
+    DCG_LAUNCH_CHECK();
+    DCG_TRY(vec_dot(p, b.r, b.r, N, S_RR, s));
+  } else {
+    DCG_TRY(vec_zero(b.xh, N, s));
+  }
+  std::vector<double> h1(m + 1), h2(m + 1), cs(m), sn(m), g(m + 1), y(m);
+  std::vector<std::vector<double>> R(m);
+  while (!*converged && c.st->outer_its < c.max_it) {
+    DCG_TRY(read_scalars(p, s));
+    const double beta = std::sqrt(p->scal_host[S_RR]);
+    if (!std::isfinite(beta)) {
+      c.st->status = DCG_ERR_BREAKDOWN;
+      break;
+    }
+    if (beta <= c.eps) {
+      *converged = true;
+      break;
+    }
+    k_scale_to<<<grid_n(N), kRedThreads, 0, s>>>(V, b.r, 1.0 / beta, N);
+    DCG_LAUNCH_CHECK();
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    bool lucky = false;
+    while (j < m && c.st->outer_its < c.max_it) {
+      DCG_TRY(apply_md(c, V + (size_t)j * N, inner_tol(c, std::fabs(g[j])), true));
+      const int K = j + 1;
+      const dim3 grid(kMultiDotGrid, (K + kMultiDot - 1) / kMultiDot);
+      const int prof = prof_begin(p, PC_VEC, s);
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        double* hd = pass == 0 ? b.dqs : b.coef;
+        k_gs_dots<<<grid, kRedThreads, 0, s>>>(b.q, V, K, N, b.part);
+        DCG_LAUNCH_CHECK();
+        k_gs_finish<<<K, kRedThreads, 0, s>>>(b.part, kMultiDotGrid, hd);
+        DCG_LAUNCH_CHECK();
+        k_gs_update<<<grid_n(N), kRedThreads, 0, s>>>(b.q, V, hd, K, N, make_reduce(p, S_TMP0));
+        DCG_LAUNCH_CHECK();
+      }
+      prof_end(p, prof, s, 8.0 * K * N, 8.0 * N * (4.0 * K + 4.0));
+      DCG_CUDA(cudaMemcpyAsync(h1.data(), b.dqs, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+      DCG_CUDA(cudaMemcpyAsync(h2.data(), b.coef, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+      DCG_TRY(read_scalars(p, s));
+      std::vector<double> col(K + 1);
+      for (int i = 0; i < K; ++i) col[i] = h1[i] + h2[i];
+      const double hn = std::sqrt(p->scal_host[S_TMP0]);
+      col[K] = hn;
+      for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
+        const double a = col[i], bb = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * bb;
+        col[i + 1] = -sn[i] * a + cs[i] * bb;
+      }
+      const double den = std::hypot(col[j], col[j + 1]);
+      if (!(den > 0.0) || !std::isfinite(den)) {
+        c.st->status = DCG_ERR_BREAKDOWN;
+        break;
+      }
+      cs[j] = col[j] / den;
+      sn[j] = col[j + 1] / den;
+      col[j] = den;
+      col.resize(K);
+      R[j] = col;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      c.st->outer_its++;
+      if (hn > 0.0) {
+        k_scale_to<<<grid_n(N), kRedThreads, 0, s>>>(V + (size_t)K * N, b.q, 1.0 / hn, N);
+        DCG_LAUNCH_CHECK();
+      } else {
+        lucky = true;
+      }
+      ++j;
+      if (std::fabs(g[j]) <= c.eps || lucky) {
+        *converged = true;
+        break;
+      }
+    }
+    if (j > 0) {
+      for (int i = j - 1; i >= 0; --i) {  // R y = g by back substitution
+        double v = g[i];
+        for (int k = i + 1; k < j; ++k) v -= R[k][i] * y[k];
+        y[i] = v / R[i][i];
+      }
+      DCG_CUDA(cudaMemcpyAsync(b.coef, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+      k_multi_axpy<<<grid_n(N), kRedThreads, 0, s>>>(b.xh, V, b.coef, j, N);
+      DCG_LAUNCH_CHECK();
+      DCG_CUDA(cudaStreamSynchronize(s));  // y is a host array
+    }
+    if (*converged || c.st->status != DCG_OK) break;
+    // restart: r = f_D - M_D x_hat
+    DCG_TRY(apply_md(c, b.xh, tc0, false));
+    DCG_TRY(spmv_f_minus_avz(p, f, b.zf, b.r, S_RR, s));
+    k_sub<<<grid_n(N), kRedThreads, 0, s>>>(b.r, b.q, N);
+    DCG_LAUNCH_CHECK();
+    DCG_TRY(vec_dot(p, b.r, b.r, N, S_RR, s));
+  }
+  DCG_TRY(pi_of_Ax(c, b.xh, b.zh, tc0, false));
+  return solver_reconstruct(p, b.xh, b.zh, b.zf, x, s);
+}
+
 int plain_cg(Ctx& c, const double* f, double* x) {
   dcg_problem* p = c.p;
   SolverBuffers& b = p->sb;
@@ -487,7 +694,10 @@ int solve_device(dcg_problem* p, const double* f, double* x, double tol, int max
   Ctx c{p, s, st, tol, 0.0, 0.0, max_it, R_CG};
   const dcg_options& o = p->opts;
   if (o.deflate) {
-    c.rule = o.recurrence == DCG_FR ? R_FR : (o.recurrence == DCG_FCG_INF ? R_FCGINF : R_FCG1);
+    c.rule = o.recurrence == DCG_FR ? R_FR
+             : o.recurrence == DCG_FCG_INF ? R_FCGINF
+             : o.recurrence == DCG_GMRES ? R_GMRES
+                                          : R_FCG1;
   }
   const long long N = p->N;
   SolverBuffers& b = p->sb;
@@ -515,9 +725,10 @@ int solve_device(dcg_problem* p, const double* f, double* x, double tol, int max
   if (!o.deflate) {
     DCG_TRY(plain_cg(c, f, x));
   } else {
-    if (c.rule == R_FCGINF && !b.dirs) return DCG_ERR_STATE;
+    if ((c.rule == R_FCGINF || c.rule == R_GMRES) && !b.dirs) return DCG_ERR_STATE;
     bool conv = false;
-    DCG_TRY(fdcg_pass(c, f, x, x0_nonzero, &conv, &stalled));
+    if (c.rule == R_GMRES) DCG_TRY(gmres_pass(c, f, x, x0_nonzero, &conv));
+    else DCG_TRY(fdcg_pass(c, f, x, x0_nonzero, &conv, &stalled));
   }
   // true residual
   DCG_TRY(spmv_residual(p, f, x, b.u, S_TMP0, s));
@@ -530,7 +741,8 @@ int solve_device(dcg_problem* p, const double* f, double* x, double tol, int max
       if (!stalled) ++claimed;
       st->restarts++;
       bool conv = false;
-      DCG_TRY(fdcg_pass(c, b.u, b.e, false, &conv, &stalled));
+      if (c.rule == R_GMRES) DCG_TRY(gmres_pass(c, b.u, b.e, false, &conv));
+      else DCG_TRY(fdcg_pass(c, b.u, b.e, false, &conv, &stalled));
       DCG_TRY(solver_axpy(p, x, b.e, s));
       DCG_TRY(spmv_residual(p, f, x, b.u, S_TMP0, s));
       DCG_TRY(read_scalars(p, s));

@@ -26,7 +26,7 @@ DCG_ERR_UNSUPPORTED = 6
 DCG_ERR_STATE = 7
 
 DCG_INNER_FIXED, DCG_INNER_ADAPTIVE, DCG_INNER_EXACT = 0, 1, 2
-DCG_FCG1, DCG_FR, DCG_FCG_INF = 0, 1, 2
+DCG_FCG1, DCG_FR, DCG_FCG_INF, DCG_GMRES = 0, 1, 2, 3
 DCG_FP64, DCG_MIXED = 0, 1
 DCG_INV_FP32, DCG_INV_BF16 = 0, 1
 DCG_RAS_MULTIPLICITY, DCG_RAS_RESTRICTED = 0, 1

@@ -266,3 +266,39 @@ def test_fma_rate_diagnostic():
     r64 = dcg.dcg_measure_fma_rate(dcg.DCG_FP64)
     r32 = dcg.dcg_measure_fma_rate(dcg.DCG_MIXED)
     assert r64 > 0.1 and r32 > 10 * r64
+
+
+# --------------------------------------------------------------------------- GMRES outer solver
+
+
+@pytest.mark.parametrize("d,n,dt,rule,m", [(2, 32, 1e-4, "fixed", None), (2, 32, 1e-2, "adaptive", None),
+                                           (3, 8, 1e-4, "adaptive", None), (2, 24, 1e-3, "fixed", 5)])
+def test_gmres_against_oracle(d, n, dt, rule, m):
+    """GMRES on the deflated system (remarks in Sections 4.3 and 5.1): the
+    device's classical Gram-Schmidt applied twice against the oracle's
+    modified Gram-Schmidt, full and restarted."""
+    o = mg.MGOptions()
+    asm = fem.assemble(d, n, dt)
+    f = inputs.rhs(4, asm.mesh.n_unknowns)
+    prob = dcg.dcg_assemble(d, n, dt)
+    rules = {"fixed": dcg.DCG_INNER_FIXED, "adaptive": dcg.DCG_INNER_ADAPTIVE}
+    dcg.dcg_setup(prob, gpu_opts(o, recurrence=dcg.DCG_GMRES, inner_rule=rules[rule], c=0.05, fcg_max_dirs=m or 0))
+    x = torch.zeros(prob.N, dtype=torch.float64, device="cuda")
+    st = dcg.dcg_solve(prob, dev(f), x, tol=1e-8)
+    x_o, st_o = solvers.FDCG(asm, solvers.FDCGOptions(mg=o, recurrence="gmres", inner_rule=rule, c=0.05,
+                                                      m_max=m)).solve(f)
+    assert st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8 and st_o.converged
+    assert abs(st["outer_its"] - st_o.outer_its) <= 2, (st["outer_its"], st_o.outer_its)
+    assert relerr(host(x), x_o) <= 1e-7
+
+
+def test_gmres_converges_where_fcg1_breaks_down():
+    o = mg.MGOptions(patch=4, overlap=1, max_levels=2)
+    asm = fem.assemble(2, 12, 0.1)
+    f = inputs.rhs(5, asm.mesh.n_unknowns)
+    prob = dcg.dcg_assemble(2, 12, 0.1)
+    dcg.dcg_setup(prob, gpu_opts(o, recurrence=dcg.DCG_GMRES, inner_rule=dcg.DCG_INNER_ADAPTIVE, c=0.2,
+                                 fcg_max_dirs=400))
+    x = torch.zeros(prob.N, dtype=torch.float64, device="cuda")
+    st = dcg.dcg_solve(prob, dev(f), x, tol=1e-8, max_it=400)
+    assert st["status"] == dcg.DCG_OK and st["true_relres"] <= 1e-8 and st["outer_its"] < 400

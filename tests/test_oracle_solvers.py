@@ -265,3 +265,43 @@ def test_fcg1_breaks_down_where_fcg_inf_does_not():
     assert s1.breakdown and not s1.converged and s1.outer_its < 400
     assert not si.breakdown and si.outer_its == 400
     assert si.true_relres < 0.1 * s1.true_relres
+
+
+def test_gmres_minimal_residual_with_exact_inner():
+    """With exact inner solves the deflated operator is fixed and SPD: GMRES
+    minimises the residual 2-norm over the Krylov space, so its residual at
+    every step is at most CG's (FCG(inf) = CG here), and it converges."""
+    asm = fem.assemble(2, 16, 1e-4)
+    f = _f(asm, seed=1)
+    _, sg = solvers.FDCG(asm, solvers.FDCGOptions(recurrence="gmres", inner_rule="exact")).solve(f, tol=1e-10)
+    _, sc = solvers.FDCG(asm, solvers.FDCGOptions(recurrence="fcg_inf", inner_rule="exact")).solve(f, tol=1e-10)
+    assert sg.converged and sg.true_relres <= 1e-10
+    k = min(len(sg.history), len(sc.history))
+    assert np.all(np.array(sg.history[:k]) <= np.array(sc.history[:k]) * (1 + 1e-10))
+    assert sg.outer_its <= sc.outer_its
+
+
+def test_gmres_restart_special_cases():
+    """GMRES(m) with m beyond the iteration count is full GMRES bit for bit; a
+    short restart still converges (the restarts begin from f_D - M_D x_hat)."""
+    asm = fem.assemble(2, 16, 1e-5)
+    f = _f(asm, seed=2)
+    xf, sf = solvers.FDCG(asm, solvers.FDCGOptions(recurrence="gmres")).solve(f)
+    xb, sb = solvers.FDCG(asm, solvers.FDCGOptions(recurrence="gmres", m_max=10 * sf.outer_its)).solve(f)
+    assert sb.history == sf.history and np.array_equal(xb, xf)
+    x4, s4 = solvers.FDCG(asm, solvers.FDCGOptions(recurrence="gmres", m_max=4)).solve(f)
+    assert s4.converged and s4.outer_its > sf.outer_its
+    assert np.linalg.norm(x4 - xf) <= 1e-6 * np.linalg.norm(xf)
+
+
+def test_gmres_converges_where_fcg1_breaks_down():
+    """Remark after Table 4: GMRES with the adaptive inner tolerance
+    converges where FCG(1) breaks down (the case of
+    test_fcg1_breaks_down_where_fcg_inf_does_not)."""
+    asm = fem.assemble(2, 12, 0.1)
+    f = inputs.rhs(5, asm.mesh.n_unknowns)
+    o = mg.MGOptions(patch=4, overlap=1, max_levels=2)
+    x, st = solvers.FDCG(asm, solvers.FDCGOptions(mg=o, recurrence="gmres", inner_rule="adaptive", c=0.2,
+                                                  max_restarts=3)).solve(f, max_it=400)
+    assert st.converged and not st.breakdown and st.outer_its < 400
+    assert np.linalg.norm(f - asm.matrix() @ x) <= 1e-8 * np.linalg.norm(f)
