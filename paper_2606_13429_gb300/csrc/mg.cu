@@ -290,36 +290,48 @@ __global__ void k_residual(Stencil<T> st, const T* __restrict__ f, const T* __re
   }
 }
 
-// coarse[I] = sum_al w(al) fine[2I+1+al]  (P^T)
+// coarse[I] = sum_al w(al) fine[2I+1+al]  (P^T), weights 1, 1/2, 1/4, 1/8:
+// per axis the line is folded as f[c] + (f[c-1] + f[c+1]) / 2 (exact
+// scalings by powers of two), which takes 2 operations per axis instead of
+// 3 multiply-adds (every fine index 2I+1+al lies inside the fine grid)
 template <typename T, int D>
 __global__ void k_restrict(const T* __restrict__ fine, T* __restrict__ coarse, int mf, int mc, long long nc) {
+  const long long sy = mf, sz = (long long)mf * mf;
   for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < nc; I += (long long)gridDim.x * blockDim.x) {
     int c[3];
     coords_of<D>(I, mc, c);
-    T acc = 0;
-    for (int az = (D > 2 ? -1 : 0); az <= (D > 2 ? 1 : 0); ++az)
-      for (int ay = -1; ay <= 1; ++ay)
-        for (int ax = -1; ax <= 1; ++ax) {
-          const int fx = 2 * c[0] + 1 + ax, fy = 2 * c[1] + 1 + ay, fz = D > 2 ? 2 * c[2] + 1 + az : 0;
-          const T w = (T)((ax ? 0.5 : 1.0) * (ay ? 0.5 : 1.0) * (az ? 0.5 : 1.0));
-          acc += w * fine[fx + (long long)mf * fy + (long long)mf * mf * fz];
-        }
-    coarse[I] = acc;
+    const long long base = (2 * c[0] + 1) + sy * (2 * c[1] + 1) + (D > 2 ? sz * (2 * c[2] + 1) : 0);
+    T plane[3];
+#pragma unroll
+    for (int az = 0; az < (D > 2 ? 3 : 1); ++az) {
+      T row[3];
+#pragma unroll
+      for (int ay = 0; ay < 3; ++ay) {
+        const T* f = fine + base + (ay - 1) * sy + (D > 2 ? (az - 1) * sz : 0);
+        row[ay] = fma((T)0.5, f[-1] + f[1], f[0]);
+      }
+      plane[az] = fma((T)0.5, row[0] + row[2], row[1]);
+    }
+    coarse[I] = D > 2 ? fma((T)0.5, plane[0] + plane[2], plane[1]) : plane[0];
   }
 }
 
-// fine[a] += sum_I P[a][I] coarse[I]
+// fine[a] += sum_I P[a][I] coarse[I]: per axis an odd fine index sits on coarse
+// node (c-1)/2 (weight 1), an even one between c/2-1 and c/2 (weight 1/2
+// each, a missing boundary neighbour contributing 0); the coarse values are
+// summed first and scaled once by 2^-(number of even axes), exactly
 template <typename T, int D>
 __global__ void k_prolong_add(const T* __restrict__ coarse, T* __restrict__ fine, int mf, int mc, long long nf) {
   for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < nf; a += (long long)gridDim.x * blockDim.x) {
     int c[3];
     coords_of<D>(a, mf, c);
     int lo[3], cnt[3];
-    T w0[3], w1[3];
+    int halves = 0;
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-      if (k >= D) { lo[k] = 0; cnt[k] = 1; w0[k] = 1; w1[k] = 0; continue; }
-      if (c[k] & 1) { lo[k] = (c[k] - 1) >> 1; cnt[k] = 1; w0[k] = 1; w1[k] = 0; }
-      else { lo[k] = (c[k] >> 1) - 1; cnt[k] = 2; w0[k] = (T)0.5; w1[k] = (T)0.5; }
+      if (k >= D) { lo[k] = 0; cnt[k] = 1; continue; }
+      if (c[k] & 1) { lo[k] = (c[k] - 1) >> 1; cnt[k] = 1; }
+      else { lo[k] = (c[k] >> 1) - 1; cnt[k] = 2; ++halves; }
     }
     T acc = 0;
     for (int iz = 0; iz < cnt[2]; ++iz)
@@ -327,10 +339,10 @@ __global__ void k_prolong_add(const T* __restrict__ coarse, T* __restrict__ fine
         for (int ix = 0; ix < cnt[0]; ++ix) {
           const int X = lo[0] + ix, Y = lo[1] + iy, Z = lo[2] + iz;
           if (X < 0 || X >= mc || Y < 0 || Y >= mc || (D > 2 && (Z < 0 || Z >= mc))) continue;
-          const T w = (ix ? w1[0] : w0[0]) * (iy ? w1[1] : w0[1]) * (iz ? w1[2] : w0[2]);
-          acc += w * coarse[X + (long long)mc * Y + (long long)mc * mc * Z];
+          acc += coarse[X + (long long)mc * Y + (long long)mc * mc * Z];
         }
-    fine[a] += acc;
+    const T scale = halves == 0 ? (T)1 : halves == 1 ? (T)0.5 : halves == 2 ? (T)0.25 : (T)0.125;
+    fine[a] = fma(scale, acc, fine[a]);
   }
 }
 
@@ -812,8 +824,10 @@ __global__ void k_ras_update(const int* __restrict__ ysrc, const T* __restrict__
         }
     }
     // multiplicities are products of 1s and 2s (a node lies in at most two
-    // boxes per axis): their reciprocals are exact, so this equals s / mult
-    z[a] += restricted ? s : s * ((T)1 / (T)mult);
+    // boxes per axis): the reciprocal is an exact power of two, picked
+    // without a division, so this equals z + s / mult
+    const T inv = mult == 1 ? (T)1 : mult == 2 ? (T)0.5 : mult == 4 ? (T)0.25 : (T)0.125;
+    z[a] += restricted ? s : s * inv;
   }
 }
 
