@@ -226,15 +226,23 @@ def oracle_full_solves(n=32, dts=None, parallel=True):
 
 
 def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
     try:
         with open("/proc/cpuinfo") as fh:
             for line in fh:
                 if line.lower().startswith(("model name", "cpu model")):
                     return line.split(":", 1)[1].strip()
-        import platform
-        return platform.processor() or platform.machine()
     except Exception:
-        return "unknown"
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 # --------------------------------------------------------------------------- main arm
