@@ -156,8 +156,13 @@ typedef struct {
                             previous ones of their pass (m_i < i) */
 } dcg_stats;
 
+/* Fills opts with the defaults given in brackets above (Algorithm 2's inputs
+ * as the paper's 2D experiments set them: W-cycle, m1 = m2 = 2, c_F = 0.01). */
 void dcg_default_options(dcg_options* opts);
+/* Name of a DCG_* status code (static string; no counterpart in the paper). */
 const char* dcg_status_string(int status);
+/* Message of the last failing call on the calling thread (the failing CUDA
+ * call for DCG_ERR_CUDA); no counterpart in the paper. */
 const char* dcg_last_error(void);
 
 /* Assemble A on the current device (Section 3.1 block structure; forms of
@@ -178,7 +183,11 @@ int dcg_assemble(const dcg_mesh* mesh, double dt, double nu, const double* nu_el
  * and the coarsest exact solver. May be called again with new options. */
 int dcg_setup(dcg_problem* p, const dcg_options* opts, void* stream);
 
-/* Solve A x = f to ||f - A x|| <= tol ||f|| (true residual, FP64).
+/* Solve A x = f to ||f - A x|| <= tol ||f|| (true residual, FP64): with
+ * deflate = 1 the flexible deflated CG of Algorithm 2 (outer FCG of
+ * Algorithm 1 or GMRES, stop rule of Section 4.1 on the recursive deflated
+ * residual, reconstruction Eq. x_defl), with deflate = 0 plain CG (the CG
+ * column of Table 2).
  * f_dev, x_dev: device arrays of N doubles; x_dev holds the initial guess on
  * entry and the solution on exit. A deflated pass that ends above tol (its
  * recursion converged, or stalled: see dcg_options.stall_window) is
@@ -188,8 +197,10 @@ int dcg_setup(dcg_problem* p, const dcg_options* opts, void* stream);
 int dcg_solve(dcg_problem* p, const double* f_dev, double* x_dev, double tol,
               int max_it, dcg_stats* stats, void* stream);
 
-/* Same as dcg_solve with host arrays: copies f to the device, solves from
- * x0 = x_host, copies the solution back into x_host (all on `stream`). */
+/* Same as dcg_solve (Algorithm 2) with host arrays: copies f to the device,
+ * solves from x0 = x_host, copies the solution back into x_host (all on
+ * `stream`; the device staging vectors of 2 N doubles are allocated on the
+ * first call and kept until dcg_destroy). */
 int dcg_solve_host(dcg_problem* p, const double* f_host, double* x_host, double tol,
                    int max_it, dcg_stats* stats, void* stream);
 
@@ -226,6 +237,9 @@ int dcg_solve_batched(int nprob, dcg_problem* const* probs, int nrhs,
 int dcg_autotune(dcg_problem* p, const dcg_options* base, const double* f_dev, double inner_tol,
                  int reps, dcg_options* best, double* best_ms, void* stream);
 
+/* Frees everything dcg_assemble and dcg_setup allocated for the problem
+ * (the operator of Section 3.1, the hierarchy of Algorithm 2's set-up, the
+ * solver vectors, captured graphs); NULL is ignored. */
 void dcg_destroy(dcg_problem* p);
 
 /* ---- queries and test hooks (same kernels as the solver) --------------- */
@@ -243,7 +257,9 @@ int dcg_level_nodes(const dcg_problem* p, int level, long long* nodes);
 int dcg_export_pattern(const dcg_problem* p, int* row_ptr, int* col_idx);
 int dcg_export_values(const dcg_problem* p, double* values);
 
-/* y = A x (FP64, device arrays of N). */
+/* y = A x with the assembled operator A = M_dev/dt + K_div (Section 3.1
+ * block structure, the paper's A* = M + dt A divided by dt), FP64, device
+ * arrays of N; or the matrix-free element-by-element product. */
 int dcg_spmv(const dcg_problem* p, const double* x_dev, double* y_dev, void* stream);
 
 /* y = A x with the arithmetic of `precision`: DCG_FP64, or DCG_MIXED for
@@ -255,7 +271,10 @@ int dcg_spmv(const dcg_problem* p, const double* x_dev, double* y_dev, void* str
  * projection, reconstruction and true residual in FP64. */
 int dcg_spmv_prec(const dcg_problem* p, const double* x_dev, double* y_dev, int precision, void* stream);
 
-/* q = V^T y (N -> n_nodes) and y = V q (n_nodes -> N), device arrays. */
+/* Deflation space of Eq. Vmatrix, V = (1/sqrt d)(v kron I) with v the
+ * indicator of the diagonal components: q = V^T y (N -> n_nodes) and
+ * y = V q (n_nodes -> N), device arrays (pi(z) = V Multigrid(V^T z) in
+ * Algorithm 2). */
 int dcg_extract(const dcg_problem* p, const double* y_dev, double* q_dev, void* stream);
 int dcg_embed(const dcg_problem* p, const double* q_dev, double* y_dev, void* stream);
 

@@ -33,6 +33,23 @@ def test_header_cites_paper_passages():
         assert ref in txt, ref
 
 
+def test_every_declaration_has_its_own_comment():
+    """Each function declared in include/dcg.h is preceded by a comment of its
+    own (the passage it implements, or that it has no counterpart), not only
+    by a comment somewhere in the file."""
+    txt = open(os.path.join(ROOT, "include", "dcg.h")).read()
+    lines = txt.splitlines()
+    for name in dcg.header_functions():
+        i = next(k for k, ln in enumerate(lines) if re.search(r"\b%s\s*\(" % name, ln) and not ln.strip().startswith(("*", "/*")))
+        # walk back over other declarations of the same group to the comment
+        j = i - 1
+        while j >= 0 and not lines[j].strip().endswith("*/"):
+            assert lines[j].strip() == "" or re.match(r"^(int|void|double|const|long|#define)\b", lines[j].strip()) or \
+                lines[j].startswith(" "), (name, lines[j])
+            j -= 1
+        assert j >= 0 and i - j <= 6, name
+
+
 def test_default_options(lib):
     o = dcg.options()
     assert (o.max_levels, o.patch, o.overlap, o.m1, o.m2) == (4, 4, 1, 2, 2)
