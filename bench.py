@@ -31,6 +31,9 @@ import os
 
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
+# hardware queues for concurrent streams and graph branches (the batched
+# workload's problems run as independent branches); read at context creation
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import argparse
 import hashlib
@@ -701,13 +704,24 @@ def batched_extra(args, opts, dcg, inputs, torch):
         x.zero_()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    seq = [dcg.dcg_solve(probs[k // nrhs], fs[k], xs[k], tol=1e-8, max_it=args.max_it) for k in range(len(fs))]
+    seq, per_problem = [], [0.0] * len(probs)
+    for k in range(len(fs)):
+        tk = time.perf_counter()
+        seq.append(dcg.dcg_solve(probs[k // nrhs], fs[k], xs[k], tol=1e-8, max_it=args.max_it))
+        per_problem[k // nrhs] += time.perf_counter() - tk  # dcg_solve returns after its solve ended
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     unknowns = sum(pr.N for pr in probs) * nrhs
+    crit = max(range(len(probs)), key=lambda i: per_problem[i])
     out = {"problems": len(probs), "rhs_per_problem": nrhs, "unknowns_total": unknowns,
            "n_range": [min(n for n, _ in plist), max(n for n, _ in plist)],
            "batched_s": t_batched, "sequential_s": t_seq, "speedup": t_seq / t_batched,
+           # a problem's right-hand sides run in sequence (they share its
+           # work vectors): the slowest problem bounds the batch from below
+           "critical_path_s": per_problem[crit],
+           "critical_problem": {"n": plist[crit][0], "dt": plist[crit][1],
+                                "outer_its": [st["outer_its"] for st in seq[crit * nrhs:(crit + 1) * nrhs]]},
+           "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
            "batched_unknowns_per_s": unknowns / t_batched,
            "all_converged": code == dcg.DCG_OK and all(st["true_relres"] <= 1e-8 for st in stats),
            "same_iterations_as_sequential": all(a["outer_its"] == b["outer_its"] for a, b in zip(stats, seq)),

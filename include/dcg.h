@@ -208,12 +208,18 @@ int dcg_solve_host(dcg_problem* p, const double* f_host, double* x_host, double 
  * f_dev[p*nrhs + r], x_dev[p*nrhs + r] are device arrays of problem p's N
  * (x in: initial guess, out: solution). Problems may differ in dim, n, dt and
  * options; each must have been set up and may appear only once. The problems
- * are independent, so they run concurrently: up to 16 host workers, each with
- * its own non-blocking stream, take problems from a shared counter and solve
- * that problem's right-hand sides in turn (every pair stops at its own
- * convergence test). The work starts after what is already queued on
- * `stream` and `stream` waits for all of it; the call returns when every
- * solve has ended. stats: nprob*nrhs entries, filled per pair. Returns
+ * are independent, so they run concurrently. When every problem's solve can
+ * be captured (dcg_options.device_loop = 1, deflated CG with W-cycle inner
+ * solves, no kernel-class timing) the whole batch is captured into one CUDA
+ * graph, a branch per problem with its pairs in sequence, every pair stopping
+ * at its own device-side convergence test, and launched once: no host read
+ * inside the batch. The branches run on as many hardware queues as
+ * CUDA_DEVICE_MAX_CONNECTIONS allows (8 unless set before the first CUDA
+ * call; 32 lets a large batch overlap). Otherwise up to 16 host workers, each
+ * with its own non-blocking stream, take problems from a shared counter and
+ * solve that problem's right-hand sides in turn with the host-driven loop.
+ * The work starts after what is already queued on `stream` and `stream`
+ * waits for all of it; the call returns when every solve has ended. stats: nprob*nrhs entries, filled per pair. Returns
  * DCG_OK if every pair converged, else the first non-OK pair status, or the
  * first hard error (DCG_ERR_CUDA, ...) a worker met. */
 int dcg_solve_batched(int nprob, dcg_problem* const* probs, int nrhs,

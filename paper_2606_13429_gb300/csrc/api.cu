@@ -351,7 +351,8 @@ int dcg_solve_batched(int nprob, dcg_problem* const* probs, int nrhs, const doub
   }
   if (nprob == 0) return DCG_OK;
   bool graph_ok = true;
-  for (int i = 0; i < nprob; ++i) graph_ok = graph_ok && graph_solve_supported(probs[i]);
+  for (int i = 0; i < nprob; ++i)
+    graph_ok = graph_ok && graph_solve_supported(probs[i]);
   if (graph_ok) {
     // one CUDA graph for the whole batch: every pair stops at its own
     // device-side convergence test, problems run as independent branches

@@ -161,6 +161,10 @@ struct Level {
   long long nn = 0;                 // m^d nodes
   Stencil<double> st64{};
   Stencil<float> st32{};
+  // 2D stencil with 8 equal neighbour coefficients (the Q1 Laplacian):
+  // Z z = box_c0 z + box_c1 (3 x 3 box sum), box_c0 = centre - box_c1
+  bool box = false;
+  double box_c0 = 0.0, box_c1 = 0.0;
   // RAS
   Tiles1D tiles{};
   int npatch = 0, nclass = 0, npmax = 0;
@@ -198,8 +202,12 @@ struct Coarse {
   int m = 0;          // interior nodes per axis on the coarsest level
   double* S64 = nullptr;   // m x m orthonormal sine matrix
   float* S32 = nullptr;
-  double* lam64 = nullptr; // eigenvalues of Z_1 (m^d)
-  float* lam32 = nullptr;
+  // line solves along the last axis. FFT route (m = 2^q - 1): cyclic
+  // reduction, tri_l = beta_k, tri_w = gamma_k ([q][m^(d-1)] each), tri_e
+  // unused. Dense route: Thomas multipliers l and reciprocal pivots 1/w (m^d
+  // each, layout of the data) and off-diagonals e (m^(d-1))
+  double *tri_l64 = nullptr, *tri_w64 = nullptr, *tri_e64 = nullptr;
+  float *tri_l32 = nullptr, *tri_w32 = nullptr, *tri_e32 = nullptr;
   void* tmp = nullptr;     // work vector (m^d, precision of the cycle)
   // FFT route when m + 1 is a power of two: log2(2(m+1)) (0: dense passes)
   // and the twiddles e^{-2 pi i j / (2(m+1))}, j < m + 1
@@ -307,6 +315,9 @@ constexpr int kNumCounters = 8;
 inline Reduce make_reduce(dcg_problem* p, int slot, int counter = 0) {
   return Reduce{p->partials, p->counters + counter, p->scal + slot};
 }
+
+// 16-byte aligned (vector loads of two doubles allowed)
+inline bool aligned16(const void* p) { return (reinterpret_cast<unsigned long long>(p) & 15ull) == 0; }
 
 inline int grid_for(long long n, int threads, int cap = kMaxRedCtas) {
   long long g = (n + threads - 1) / threads;

@@ -20,10 +20,12 @@
 //
 // Coarsest level (Algorithm 4, k = 1): exact solve by fast diagonalisation:
 // Z_1 = (1/d) sum_i (x)_ax {K1 if ax = i else M1} with 1D Q1 matrices
-// K1, M1 diagonalised by the orthonormal sine basis S, so
-// Z_1^-1 = (S (x) .. (x) S) Lambda^-1 (S (x) .. (x) S); applied as 2d passes
-// of S along one axis. The coarse Galerkin stencil is checked against that
-// closed form before use.
+// K1, M1 diagonalised by the orthonormal sine basis S. Transformed by S
+// along every axis but the last, Z_1 falls apart into independent
+// tridiagonal systems along the last axis, one per transformed line, so
+// Z_1^-1 = (S (x) .. (x) S (x) I) T^-1 (S (x) .. (x) S (x) I): d - 1 passes of
+// S, one pass of line solves, d - 1 passes of S. The coarse Galerkin stencil
+// is checked against the closed form before use.
 //
 // W-cycle recursion (Algorithm 4) runs in the set-up precision (FP32 in
 // mixed mode, FP64 otherwise) and is captured once into a CUDA graph. The
@@ -44,6 +46,9 @@ namespace {
 
 constexpr int kKC = 32;       // K chunk of the inverse staged in shared memory
 constexpr int kFdmBatch = 16; // boxes per work item of the fast-diagonalisation smoother
+// boxes per work item of the tensor-core smoother: rows of the M = 128 MMA
+// beyond them are zero; smaller items spread a level over more SMs
+constexpr int kTcBatch = 64;
 constexpr int kFdmThreads = 192;
 constexpr int kRasThreads = 256;
 constexpr int kMaxNp = 256;   // largest box (nodes) supported
@@ -187,35 +192,111 @@ __global__ void k_sym_convert(const double* __restrict__ a, T* __restrict__ out,
   out[t] = j < n ? (T)(0.5 * (a[(long long)i * n + j] + a[(long long)j * n + i])) : (T)0;
 }
 
-// sine basis S[i][j] = sqrt(2/(m+1)) sin((i+1)(j+1) pi/(m+1)) and eigenvalues
-template <int D>
-__global__ void k_fdm_setup(int m, double* __restrict__ S, double* __restrict__ lam) {
+// sine basis S[i][j] = sqrt(2/(m+1)) sin((i+1)(j+1) pi/(m+1))
+__global__ void k_fdm_setup(int m, double* __restrict__ S) {
   const int n1 = m + 1;
-  const double h = 1.0 / n1;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t < (long long)m * m) {
     int i = (int)(t / m), j = (int)(t % m);
     long long ij = (long long)(i + 1) * (j + 1) % (2 * n1);
     S[t] = sqrt(2.0 / n1) * sin(M_PI * (double)ij / n1);
   }
-  long long nn = 1;
-  for (int k = 0; k < D; ++k) nn *= m;
-  if (t < nn) {
-    int jj[3] = {(int)(t % m), (int)((t / m) % m), D > 2 ? (int)(t / ((long long)m * m)) : 0};
-    double kap[3], mu[3];
-    for (int k = 0; k < D; ++k) {
-      double th = M_PI * (jj[k] + 1) / n1;
-      kap[k] = (2.0 / h) * (1.0 - cos(th));
-      mu[k] = (h / 3.0) * (2.0 + cos(th));
-    }
-    double l = 0.0;
-    for (int i = 0; i < D; ++i) {
-      double term = kap[i];
-      for (int k = 0; k < D; ++k)
-        if (k != i) term *= mu[k];
-      l += term;
-    }
-    lam[t] = l / D;
+}
+
+// Line-solve factors of the coarsest solve along the last axis. With the
+// sine indices j_k of a line on the other d - 1 axes (kappa_k = (2/h)(1 -
+// cos th_k), mu_k = (h/3)(2 + cos th_k), th_k = pi (j_k + 1) / (m + 1): the
+// eigenvalues of K1 and M1), Z_1 restricted to the transformed line is
+//   T_j = a_j M1 + b_j K1,  a_j = (1/d) sum_i kappa_i prod_{k != i} mu_k,
+//                           b_j = (1/d) prod_k mu_k,
+// tridiagonal, symmetric and Toeplitz with diagonal a (2h/3) + b (2/h) and
+// off-diagonal e = a h/6 - b/h, strictly diagonally dominant (a, b > 0).
+// Tabulated per line: the elimination multipliers l_y = e / w_{y-1} (l_0 = 0)
+// and the reciprocal pivots 1/w_y, w_y = diagonal - l_y e, both in the
+// data's layout [y][j]; and e_j.
+template <int D>
+__global__ void k_tri_setup(int m, double* __restrict__ fl, double* __restrict__ fw, double* __restrict__ fe) {
+  long long M1 = 1;
+  for (int k = 0; k < D - 1; ++k) M1 *= m;
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= M1) return;
+  const int n1 = m + 1;
+  const double h = 1.0 / n1;
+  double kap[3], mu[3];
+  long long r = j;
+  for (int k = 0; k < D - 1; ++k) {
+    const int jk = (int)(r % m);
+    r /= m;
+    const double th = M_PI * (jk + 1) / n1;
+    kap[k] = (2.0 / h) * (1.0 - cos(th));
+    mu[k] = (h / 3.0) * (2.0 + cos(th));
+  }
+  double a = 0.0, b = 1.0;
+  for (int i = 0; i < D - 1; ++i) {
+    double t = kap[i];
+    for (int k = 0; k < D - 1; ++k)
+      if (k != i) t *= mu[k];
+    a += t;
+    b *= mu[i];
+  }
+  a /= D;
+  b /= D;
+  const double dg = a * (2.0 * h / 3.0) + b * (2.0 / h);
+  const double e = a * (h / 6.0) - b / h;
+  double w = dg;
+  fl[j] = 0.0;
+  fw[j] = 1.0 / w;
+  for (int y = 1; y < m; ++y) {
+    const double l = e / w;
+    w = dg - l * e;
+    fl[j + M1 * y] = l;
+    fw[j + M1 * y] = 1.0 / w;
+  }
+  fe[j] = e;
+}
+
+// Cyclic-reduction coefficients of the same line systems when m = 2^q - 1
+// (the FFT route). T_j is Toeplitz, tridiag(e, dg, e), with x_0 = x_{m+1} = 0;
+// eliminating the odd unknowns leaves the even ones in a Toeplitz system of
+// size 2^(q-1) - 1 with e' = -e^2/dg, dg' = dg - 2 e^2/dg, and so on down to
+// one unknown. Tabulated per level k < q, layout [k][j]: beta_k = e_k / dg_k
+// and gamma_k = 1 / dg_k.
+template <int D>
+__global__ void k_cr_setup(int m, int q, double* __restrict__ beta, double* __restrict__ gamma) {
+  long long M1 = 1;
+  for (int k = 0; k < D - 1; ++k) M1 *= m;
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= M1) return;
+  const int n1 = m + 1;
+  const double h = 1.0 / n1;
+  double kap[3], mu[3];
+  long long r = j;
+  for (int k = 0; k < D - 1; ++k) {
+    const int jk = (int)(r % m);
+    r /= m;
+    const double th = M_PI * (jk + 1) / n1;
+    kap[k] = (2.0 / h) * (1.0 - cos(th));
+    mu[k] = (h / 3.0) * (2.0 + cos(th));
+  }
+  double a = 0.0, b = 1.0;
+  for (int i = 0; i < D - 1; ++i) {
+    double t = kap[i];
+    for (int k = 0; k < D - 1; ++k)
+      if (k != i) t *= mu[k];
+    a += t;
+    b *= mu[i];
+  }
+  a /= D;
+  b /= D;
+  double dg = a * (2.0 * h / 3.0) + b * (2.0 / h);
+  double e = a * (h / 6.0) - b / h;
+  for (int k = 0; k < q; ++k) {
+    const double bk = e / dg;
+    beta[k * M1 + j] = bk;
+    gamma[k * M1 + j] = 1.0 / dg;
+    const double e2 = e * bk;  // e^2 / dg
+    dg = dg - 2.0 * e2;
+    e = -e2;
   }
 }
 
@@ -288,6 +369,60 @@ __global__ void k_residual(Stencil<T> st, const T* __restrict__ f, const T* __re
     coords_of<D>(a, m, c);
     y[a] = f[a] - stencil_apply<T, D>(st, z, m, c);
   }
+}
+
+// 2D levels whose 8 neighbour coefficients are equal (the Q1 Laplacian):
+//   (Z z)_a = c1 (sum of the 3 x 3 box around a) + (c_centre - c1) z_a,
+// with the box sum formed from row sums s(y) = z(x-1,y) + z(x,y) + z(x+1,y)
+// that slide along y: a residual takes 4 additions and 2 FMAs per node
+// instead of 9 FMAs and a subtraction (FP64 issue is what the FP64 cycle
+// spends). A thread walks kBoxSeg rows of one column; consecutive threads
+// take consecutive columns, so every row access is coalesced. Entries
+// outside the grid are zero (Dirichlet nodes eliminated).
+constexpr int kBoxSeg = 16;
+constexpr int kBoxThreads = 128;
+
+template <typename T>
+__device__ __forceinline__ T box_row(const T* __restrict__ z, int x, int y, int m, T& centre) {
+  centre = (T)0;
+  if (y < 0 || y >= m) return (T)0;
+  const T* row = z + (long long)m * y;
+  centre = __ldg(row + x);
+  T s = centre;
+  if (x > 0) s = __ldg(row + x - 1) + s;
+  if (x + 1 < m) s = s + __ldg(row + x + 1);
+  return s;
+}
+
+// Walks rows y0 .. y0 + kBoxSeg - 1 of column x and calls
+// body(a, r_a) with r_a = f_a - (Z z)_a.
+template <typename T, typename F, typename Body>
+__device__ __forceinline__ void box_residual_walk(T c0, T c1, const F* __restrict__ f, const T* __restrict__ z, int m,
+                                                  int x, int y0, Body&& body) {
+  const int y1 = min(y0 + kBoxSeg, m);
+  T cm, c0v;
+  T sm = box_row(z, x, y0 - 1, m, cm);
+  T s0 = box_row(z, x, y0, m, c0v);
+  for (int y = y0; y < y1; ++y) {
+    T cp;
+    const T sp = box_row(z, x, y + 1, m, cp);
+    const long long a = x + (long long)m * y;
+    const T box = (sm + s0) + sp;
+    const T r = fma(-c1, box, fma(-c0, c0v, (T)__ldg(f + a)));
+    body(a, r);
+    sm = s0;
+    s0 = sp;
+    c0v = cp;
+  }
+}
+
+// y = f - Z z on a box-sum level (grid: columns / kBoxThreads x rows / kBoxSeg)
+template <typename T>
+__global__ void __launch_bounds__(kBoxThreads) k_residual_box(T c0, T c1, const T* __restrict__ f,
+                                                              const T* __restrict__ z, T* __restrict__ y, int m) {
+  const int x = blockIdx.x * kBoxThreads + threadIdx.x;
+  if (x >= m) return;
+  box_residual_walk<T, T>(c0, c1, f, z, m, x, blockIdx.y * kBoxSeg, [&](long long a, T r) { y[a] = r; });
 }
 
 // coarse[I] = sum_al w(al) fine[2I+1+al]  (P^T), weights 1, 1/2, 1/4, 1/8:
@@ -629,7 +764,7 @@ __global__ void __launch_bounds__(256) k_ras_solve_tc(RasArgs ra, const float* _
         if (box < nb) {
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            if (c + j < np) yi[(size_t)(c + j) * 128 + box] = v[j];
+            if (c + j < np) yi[(size_t)(c + j) * C.nb + box] = v[j];
         }
       }
     }
@@ -844,8 +979,7 @@ __device__ __forceinline__ void lds4(const double* p, double (&v)[4]) {
 
 // Coarsest solve pass: S applied along one axis of the level grid, as the GEMM
 //   C[i][n] = sum_k S[k][i] B[k][n],  B[k][n] = in[(n / inner) m inner + k inner + n % inner]
-// (inner = m^axis; S is symmetric, so S[k][i] = S[i][k]), with optional
-// division by the eigenvalues in the epilogue. A CTA of 128 threads owns a
+// (inner = m^axis; S is symmetric, so S[k][i] = S[i][k]). A CTA of 128 threads owns a
 // 32 x 32 tile of C, each thread a 2 x 4 register block; k runs through
 // chunks of 32 staged in two shared-memory buffers, the next chunk held in
 // registers while the current one is multiplied. The k sum runs in order
@@ -856,8 +990,8 @@ constexpr int kFdmTile = 32, kFdmLd = 36;
 
 template <typename T, bool AXIS0>
 __global__ void __launch_bounds__(128) k_fdm_pass(const T* __restrict__ in, T* __restrict__ out,
-                                                  const T* __restrict__ S, const T* __restrict__ lam, int m,
-                                                  long long inner, long long ncols) {
+                                                  const T* __restrict__ S, int m, long long inner,
+                                                  long long ncols) {
   constexpr int KC = kFdmTile, LD = kFdmLd, NT = 128, R = KC * kFdmTile / NT, KW = NT / 32;
   __shared__ __align__(16) T sA[2][KC][LD];
   __shared__ __align__(16) T sB[2][KC][LD];
@@ -934,7 +1068,7 @@ __global__ void __launch_bounds__(128) k_fdm_pass(const T* __restrict__ in, T* _
       if (nb >= ncols) continue;
       const long long hi = nb / inner;
       const long long o = hi * m * inner + (long long)ii * inner + (nb - hi * inner);
-      out[o] = lam ? acc[a][q] / lam[o] : acc[a][q];
+      out[o] = acc[a][q];
     }
   }
 }
@@ -999,15 +1133,12 @@ __device__ __forceinline__ void dst_stages(C2* buf, const C2* stw, int NP, int N
   }
 }
 
-// One pass (or, with FUSED, the two passes along the same axis around the
-// eigenvalue division: out = S (Lambda^-1 o (S in)) line by line).
-template <typename T, bool AXIS0, int COLS, bool FUSED>
+// One pass: out = S in along one axis, line by line.
+template <typename T, bool AXIS0, int COLS>
 __global__ void __launch_bounds__(256) k_dst_pass(const T* __restrict__ in, T* __restrict__ out,
-                                                  const typename cplx<T>::type* __restrict__ tw,
-                                                  const T* __restrict__ lam, int m, int log2n2, long long inner,
-                                                  long long ncols, T scale) {
+                                                  const typename cplx<T>::type* __restrict__ tw, int m, int log2n2,
+                                                  long long inner, long long ncols, T scale) {
   using C2 = typename cplx<T>::type;
-  constexpr int kMaxPer = 8;  // entries per thread kept in registers between the fused transforms
   extern __shared__ __align__(16) unsigned char dst_smem[];
   const int N2 = 1 << log2n2, N = N2 >> 1, NP = N2 + (N2 >> 5);
   C2* buf = reinterpret_cast<C2*>(dst_smem);  // [COLS / 2][NP]
@@ -1044,35 +1175,6 @@ __global__ void __launch_bounds__(256) k_dst_pass(const T* __restrict__ in, T* _
   }
   __syncthreads();
   dst_stages(buf, stw, NP, N, log2n2, COLS / 2);
-  if (FUSED) {
-    // sine sums of the first transform, divided by the eigenvalues, become
-    // the input of the second (entries held in registers across the rebuild)
-    T keep[kMaxPer];
-    int i = 0;
-    for (int t = threadIdx.x; t < total; t += blockDim.x, ++i) {
-      int c, k;
-      entry(t, c, k);
-      const long long nb = n0 + c;
-      const C2 V = buf[(c >> 1) * NP + dst_pad(k + 1)];
-      T v = ((c & 1) ? V.x : -V.y) * scale;
-      if (nb < ncols) v = v / lam[gidx(nb, k)];
-      else v = (T)0;
-      keep[i] = v;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < COLS / 2; t += blockDim.x) {
-      buf[t * NP] = C2{(T)0, (T)0};
-      buf[t * NP + 1] = C2{(T)0, (T)0};
-    }
-    i = 0;
-    for (int t = threadIdx.x; t < total; t += blockDim.x, ++i) {
-      int c, k;
-      entry(t, c, k);
-      dst_scatter(bufr, NP, N2, log2n2, c, k, keep[i]);
-    }
-    __syncthreads();
-    dst_stages(buf, stw, NP, N, log2n2, COLS / 2);
-  }
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     int c, k;
     entry(t, c, k);
@@ -1080,9 +1182,7 @@ __global__ void __launch_bounds__(256) k_dst_pass(const T* __restrict__ in, T* _
     if (nb >= ncols) continue;
     const C2 V = buf[(c >> 1) * NP + dst_pad(k + 1)];
     T v = (c & 1) ? V.x : -V.y;
-    v *= scale;  // sqrt(2/N) / 2
-    const long long o = gidx(nb, k);
-    out[o] = (!FUSED && lam) ? v / lam[o] : v;
+    out[gidx(nb, k)] = v * scale;  // scale = sqrt(2/N) / 2
   }
 }
 
@@ -1092,27 +1192,21 @@ size_t dst_smem_bytes(int log2n2) {
   return sizeof(typename cplx<T>::type) * ((COLS / 2) * (N2 + (N2 >> 5)) + N2 / 2);
 }
 
-// one DST pass (FUSED: two passes around Lambda^-1): 2 lines per CTA for long
-// transforms (enough CTAs to fill the GPU), 8 for short ones. The route takes
-// 2(m+1) <= 2048, so a CTA holds at most 2 x 1023 (or 8 x 127) entries: at
-// most 8 per thread, as the fused kernel's register copy needs.
-template <typename T, bool FUSED>
-void dst_pass(const T* in, T* out, const typename cplx<T>::type* tw, const T* lam, int m, int log2n2,
-              long long inner, long long ncols, T scale, cudaStream_t s) {
+// one DST pass: 2 lines per CTA for long transforms (enough CTAs to fill the
+// GPU), 8 for short ones. The route takes 2(m+1) <= 2048.
+template <typename T>
+void dst_pass(const T* in, T* out, const typename cplx<T>::type* tw, int m, int log2n2, long long inner,
+              long long ncols, T scale, cudaStream_t s) {
   if (log2n2 >= 9) {
     const unsigned grid = (unsigned)((ncols + 1) / 2);
     const size_t smem = dst_smem_bytes<T, 2>(log2n2);
-    if (inner == 1)
-      k_dst_pass<T, true, 2, FUSED><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, 1, ncols, scale);
-    else
-      k_dst_pass<T, false, 2, FUSED><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, inner, ncols, scale);
+    if (inner == 1) k_dst_pass<T, true, 2><<<grid, 256, smem, s>>>(in, out, tw, m, log2n2, 1, ncols, scale);
+    else k_dst_pass<T, false, 2><<<grid, 256, smem, s>>>(in, out, tw, m, log2n2, inner, ncols, scale);
   } else {
     const unsigned grid = (unsigned)((ncols + 7) / 8);
     const size_t smem = dst_smem_bytes<T, 8>(log2n2);
-    if (inner == 1)
-      k_dst_pass<T, true, 8, FUSED><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, 1, ncols, scale);
-    else
-      k_dst_pass<T, false, 8, FUSED><<<grid, 256, smem, s>>>(in, out, tw, lam, m, log2n2, inner, ncols, scale);
+    if (inner == 1) k_dst_pass<T, true, 8><<<grid, 256, smem, s>>>(in, out, tw, m, log2n2, 1, ncols, scale);
+    else k_dst_pass<T, false, 8><<<grid, 256, smem, s>>>(in, out, tw, m, log2n2, inner, ncols, scale);
   }
 }
 
@@ -1122,68 +1216,213 @@ template <typename T>
 int set_dst_smem() {
   const int big = (int)dst_smem_bytes<T, 2>(11), small = (int)dst_smem_bytes<T, 8>(8);
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, true, 2, false>, attr, big));
-  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, false, 2, false>, attr, big));
-  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, true, 2, true>, attr, big));
-  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, false, 2, true>, attr, big));
-  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, true, 8, false>, attr, small));
-  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, false, 8, false>, attr, small));
-  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, true, 8, true>, attr, small));
-  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, false, 8, true>, attr, small));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, true, 2>, attr, big));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, false, 2>, attr, big));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, true, 8>, attr, small));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, false, 8>, attr, small));
   return DCG_OK;
 }
 
-// z = S^(x)D Lambda^-1 S^(x)D f on the coarsest grid: 2D passes along
-// axes 0, 1 (with Lambda^-1), 1, 0; 3D along 0, 1, 2 (Lambda^-1), 2, 1, 0.
+// Line solves T_j x = g along the last axis of the coarsest grid (factors
+// from k_tri_setup; line j holds entries j + M1 y, y < m). The two sweeps
+// are chains of m dependent FMAs, so their latency, not their arithmetic,
+// sets the time: a CTA takes few lines (`cols`, chosen so that the grid
+// covers the SMs about twice), stages them and their factors in shared
+// memory with all its threads ([y][c] layout, loads unrolled so that many
+// are in flight), `cols` threads run the sweeps, and all threads store.
+// The backward step is one FMA on the chain:
+//   x_y = (g'_y - e x_{y+1}) / w_y = fma(-(e / w_y), x_{y+1}, g'_y / w_y).
+constexpr size_t kTriSmem = 200 * 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_last(const T* __restrict__ in, T* __restrict__ out,
+                                                  const T* __restrict__ fl, const T* __restrict__ fw,
+                                                  const T* __restrict__ fe, int m, long long M1, int cols) {
+  extern __shared__ __align__(16) unsigned char tri_smem[];
+  T* g = reinterpret_cast<T*>(tri_smem);
+  T* sl = g + (size_t)m * cols;
+  T* sw = sl + (size_t)m * cols;
+  const long long j0 = (long long)blockIdx.x * cols;
+  const int total = m * cols;
+#pragma unroll 4
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int y = t / cols, c = t - y * cols;
+    const long long j = j0 + c;
+    if (j < M1) {
+      const long long o = j + M1 * y;
+      g[t] = __ldg(in + o);
+      sl[t] = __ldg(fl + o);
+      sw[t] = __ldg(fw + o);
+    }
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c < cols && j0 + c < M1) {
+    const T e = __ldg(fe + j0 + c);
+    T prev = (T)0;  // forward: g'_y = g_y - l_y g'_{y-1}
+    for (int y = 0; y < m; ++y) {
+      const int t = y * cols + c;
+      prev = fma(-sl[t], prev, g[t]);
+      g[t] = prev;
+    }
+    T xn = (T)0;  // backward, x_m = 0
+    for (int y = m - 1; y >= 0; --y) {
+      const int t = y * cols + c;
+      const T wi = sw[t];
+      xn = fma(-(e * wi), xn, g[t] * wi);
+      g[t] = xn;
+    }
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int y = t / cols, c2 = t - y * cols;
+    const long long j = j0 + c2;
+    if (j < M1) out[j + M1 * y] = g[t];
+  }
+}
+
+// lines per CTA of k_tri_last: enough CTAs for about two per SM, at most
+// one 128-byte shared-memory row per y (conflict-free sweeps) and what the
+// staging buffer holds; 0 when even one line does not fit
+template <typename T>
+int tri_cols(int m, long long M1) {
+  if (3 * (size_t)m * sizeof(T) > kTriSmem) return 0;
+  long long cols = std::max<long long>(1, std::min<long long>((long long)(128 / sizeof(T)), M1 / (2 * 152)));
+  while (cols > 1 && 3 * (size_t)m * cols * sizeof(T) > kTriSmem) cols >>= 1;
+  return (int)cols;
+}
+
+template <typename T>
+void tri_last(const T* in, T* out, const T* fl, const T* fw, const T* fe, int m, long long M1, cudaStream_t s) {
+  const int cols = tri_cols<T>(m, M1);
+  const unsigned grid = (unsigned)((M1 + cols - 1) / cols);
+  const size_t smem = 3 * (size_t)m * cols * sizeof(T);
+  k_tri_last<T><<<grid, 256, smem, s>>>(in, out, fl, fw, fe, m, M1, cols);
+}
+
+// The same line solves by cyclic reduction when m = 2^q - 1 (coefficients
+// from k_cr_setup). A CTA takes `cols` consecutive lines, staged in shared
+// memory as [i][c] with zero rows i = 0 and i = m + 1 (the Dirichlet ends);
+// reduction step k (k = 1..q-1, h = 2^(k-1)) updates the equations at the
+// multiples of 2h, g_i += -beta_{k-1} (g_{i-h} + g_{i+h}); the last unknown
+// (i = 2^(q-1)) is g gamma_{q-1}; back-substitution level k-1 solves the odd
+// multiples of h, x_i = gamma_{k-1} g_i - beta_{k-1} (x_{i-h} + x_{i+h}).
+// 2q - 1 steps separated by barriers, each spread over all threads: no long
+// dependent chain. The CTA's coefficients are staged with its lines, so the
+// steps touch shared memory only; few lines per CTA keep the grid wide (the
+// staging loads of many CTAs are in flight together).
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_cr(const T* __restrict__ in, T* __restrict__ out,
+                                                const T* __restrict__ beta, const T* __restrict__ gamma, int m, int q,
+                                                long long M1, int cols) {
+  extern __shared__ __align__(16) unsigned char cr_smem[];
+  T* g = reinterpret_cast<T*>(cr_smem);  // [m + 2][cols]
+  T* sb = g + (size_t)(m + 2) * cols;    // beta [q][cols]
+  T* sg = sb + (size_t)q * cols;         // gamma [q][cols]
+  const long long j0 = (long long)blockIdx.x * cols;
+  const int total = m * cols;
+#pragma unroll 4
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int i = t / cols, c = t - i * cols;
+    const long long j = j0 + c;
+    g[(i + 1) * cols + c] = j < M1 ? __ldg(in + j + M1 * i) : (T)0;
+  }
+  for (int t = threadIdx.x; t < q * cols; t += blockDim.x) {
+    const int k = t / cols, c = t - k * cols;
+    const long long j = min(j0 + c, M1 - 1);
+    sb[t] = __ldg(beta + (long long)k * M1 + j);
+    sg[t] = __ldg(gamma + (long long)k * M1 + j);
+  }
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+    g[c] = (T)0;
+    g[(m + 1) * cols + c] = (T)0;
+  }
+  __syncthreads();
+  for (int k = 1; k < q; ++k) {
+    const int h = 1 << (k - 1), cnt = (1 << (q - k)) - 1;
+    for (int t = threadIdx.x; t < cnt * cols; t += blockDim.x) {
+      const int c = t % cols, i = (t / cols + 1) * 2 * h;
+      g[i * cols + c] = fma(-sb[(k - 1) * cols + c], g[(i - h) * cols + c] + g[(i + h) * cols + c], g[i * cols + c]);
+    }
+    __syncthreads();
+  }
+  {
+    const int i = 1 << (q - 1);
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) g[i * cols + c] *= sg[(q - 1) * cols + c];
+  }
+  __syncthreads();
+  for (int k = q - 1; k >= 1; --k) {
+    const int h = 1 << (k - 1), cnt = 1 << (q - k);
+    for (int t = threadIdx.x; t < cnt * cols; t += blockDim.x) {
+      const int c = t % cols, i = h * (2 * (t / cols) + 1);
+      g[i * cols + c] = fma(-sb[(k - 1) * cols + c], g[(i - h) * cols + c] + g[(i + h) * cols + c],
+                            sg[(k - 1) * cols + c] * g[i * cols + c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll 4
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int i = t / cols, c = t - i * cols;
+    const long long j = j0 + c;
+    if (j < M1) out[j + M1 * i] = g[(i + 1) * cols + c];
+  }
+}
+
+// lines per CTA of k_tri_cr: enough CTAs for about two per SM, at most one
+// 128-byte shared-memory row per i, and what the buffer holds
+template <typename T>
+int cr_cols(int m, int q, long long M1) {
+  long long cols = std::max<long long>(1, std::min<long long>((long long)(128 / sizeof(T)), M1 / (2 * 152)));
+  while (cols > 1 && (size_t)(m + 2 + 2 * q) * cols * sizeof(T) > kTriSmem) cols >>= 1;
+  return (int)cols;
+}
+
+template <typename T>
+void tri_cr(const T* in, T* out, const T* beta, const T* gamma, int m, int q, long long M1, cudaStream_t s) {
+  const int cols = cr_cols<T>(m, q, M1);
+  const unsigned grid = (unsigned)((M1 + cols - 1) / cols);
+  const size_t smem = (size_t)(m + 2 + 2 * q) * cols * sizeof(T);
+  k_tri_cr<T><<<grid, 256, smem, s>>>(in, out, beta, gamma, m, q, M1, cols);
+}
+
+// z = Z_1^-1 f on the coarsest grid: passes of S along axes 0..d-2, line
+// solves along axis d-1, passes of S along axes d-2..0 (2d - 1 launches).
 // tmp: scratch of m^D values. With log2n2 > 0 (m + 1 a power of two) the
 // passes are sine transforms by FFT, else dense GEMM passes with S.
 // Returns the number of kernels launched.
 template <typename T, int D>
-int fdm_passes(const T* f, T* z, T* tmp, const T* S, const T* lam, const typename cplx<T>::type* tw, int log2n2,
-               int m, cudaStream_t s) {
+int fdm_passes(const T* f, T* z, T* tmp, const T* S, const T* fl, const T* fw, const T* fe,
+               const typename cplx<T>::type* tw, int log2n2, int m, cudaStream_t s) {
+  // FFT route (m + 1 = 2^(log2n2 - 1)): fl, fw hold the cyclic-reduction
+  // beta and gamma tables (fe unused); dense route: Thomas factors
   long long nn = 1;
   for (int k = 0; k < D; ++k) nn *= m;
-  const long long ncols = nn / m;
-  const long long in1 = 1, inm = m, inmm = (long long)m * m;
-  const T* src[6];
-  T* dst[6];
-  long long inner[6];
-  const T* lm[6];
+  const long long ncols = nn / m, M1 = nn / m;
+  const T scale = (T)(0.5 * std::sqrt(2.0 / (m + 1)));
+  const dim3 ggrid((unsigned)((ncols + kFdmTile - 1) / kFdmTile), (unsigned)((m + kFdmTile - 1) / kFdmTile));
+  auto pass = [&](const T* in, T* out, int axis) {
+    const long long inner = axis == 0 ? 1 : (axis == 1 ? (long long)m : (long long)m * m);
+    if (log2n2 > 0) dst_pass<T>(in, out, tw, m, log2n2, inner, ncols, scale, s);
+    else if (inner == 1) k_fdm_pass<T, true><<<ggrid, 128, 0, s>>>(in, out, S, m, 1, ncols);
+    else k_fdm_pass<T, false><<<ggrid, 128, 0, s>>>(in, out, S, m, inner, ncols);
+  };
+  auto lines = [&](const T* in, T* out) {
+    if (log2n2 > 0) tri_cr<T>(in, out, fl, fw, m, log2n2 - 1, M1, s);
+    else tri_last<T>(in, out, fl, fw, fe, m, M1, s);
+  };
   if (D == 2) {
-    const T* s2[4] = {f, tmp, z, tmp};
-    T* d2[4] = {tmp, z, tmp, z};
-    const long long i2[4] = {in1, inm, inm, in1};
-    for (int k = 0; k < 4; ++k) { src[k] = s2[k]; dst[k] = d2[k]; inner[k] = i2[k]; lm[k] = k == 1 ? lam : nullptr; }
+    pass(f, z, 0);
+    lines(z, tmp);
+    pass(tmp, z, 0);
   } else {
-    const T* s3[6] = {f, tmp, z, tmp, z, tmp};
-    T* d3[6] = {tmp, z, tmp, z, tmp, z};
-    const long long i3[6] = {in1, inm, inmm, inmm, inm, in1};
-    for (int k = 0; k < 6; ++k) { src[k] = s3[k]; dst[k] = d3[k]; inner[k] = i3[k]; lm[k] = k == 2 ? lam : nullptr; }
+    pass(f, z, 0);
+    pass(z, tmp, 1);
+    lines(tmp, z);
+    pass(z, tmp, 1);
+    pass(tmp, z, 0);
   }
-  if (log2n2 > 0) {
-    // the two passes along the last axis, around Lambda^-1, run as one
-    // kernel: 2D axes 0, 1+1, 0 and 3D 0, 1, 2+2, 1, 0 (2D - 1 launches)
-    const T scale = (T)(0.5 * std::sqrt(2.0 / (m + 1)));
-    if (D == 2) {
-      dst_pass<T, false>(f, z, tw, nullptr, m, log2n2, in1, ncols, scale, s);
-      dst_pass<T, true>(z, tmp, tw, lam, m, log2n2, inm, ncols, scale, s);
-      dst_pass<T, false>(tmp, z, tw, nullptr, m, log2n2, in1, ncols, scale, s);
-    } else {
-      dst_pass<T, false>(f, z, tw, nullptr, m, log2n2, in1, ncols, scale, s);
-      dst_pass<T, false>(z, tmp, tw, nullptr, m, log2n2, inm, ncols, scale, s);
-      dst_pass<T, true>(tmp, z, tw, lam, m, log2n2, inmm, ncols, scale, s);
-      dst_pass<T, false>(z, tmp, tw, nullptr, m, log2n2, inm, ncols, scale, s);
-      dst_pass<T, false>(tmp, z, tw, nullptr, m, log2n2, in1, ncols, scale, s);
-    }
-    return 2 * D - 1;
-  } else {
-    const dim3 grid((unsigned)((ncols + kFdmTile - 1) / kFdmTile), (unsigned)((m + kFdmTile - 1) / kFdmTile));
-    for (int k = 0; k < 2 * D; ++k) {
-      if (inner[k] == 1) k_fdm_pass<T, true><<<grid, 128, 0, s>>>(src[k], dst[k], S, lm[k], m, 1, ncols);
-      else k_fdm_pass<T, false><<<grid, 128, 0, s>>>(src[k], dst[k], S, lm[k], m, inner[k], ncols);
-    }
-  }
-  return 2 * D;
+  return 2 * D - 1;
 }
 
 // FP64 fine residual r = g - Z_J z, stored into the cycle's level-J RHS (in
@@ -1208,6 +1447,33 @@ __global__ void k_inner_residual(Stencil<double> st, const double* __restrict__ 
     if (r64) r64[a] = r;
     rr = fma(rt, rt, rr);
     if (with_g) part[1] = fma(ga, ga, part[1]);
+  }
+  part[0] = (double)rr;
+  grid_reduce<2>(part, red);
+}
+
+// k_inner_residual on a 2D box-sum level; a 1D grid of column blocks x row
+// segments (bx fastest), so that the grid reduction sees gridDim.x CTAs
+template <typename T>
+__global__ void __launch_bounds__(kBoxThreads) k_inner_residual_box(double c0, double c1, const double* __restrict__ g,
+                                                                    const double* __restrict__ z, T* __restrict__ fJ,
+                                                                    T* __restrict__ zJ, int m, int gx, Reduce red,
+                                                                    bool with_g) {
+  double part[2] = {0.0, 0.0};
+  T rr = (T)0;
+  const int bx = blockIdx.x % gx, by = blockIdx.x / gx;
+  const int x = bx * kBoxThreads + threadIdx.x;
+  if (x < m) {
+    box_residual_walk<double, double>(c0, c1, g, z, m, x, by * kBoxSeg, [&](long long a, double r) {
+      const T rt = (T)r;
+      fJ[a] = rt;
+      zJ[a] = (T)0;
+      rr = fma(rt, rt, rr);
+      if (with_g) {
+        const double ga = __ldg(g + a);
+        part[1] = fma(ga, ga, part[1]);
+      }
+    });
   }
   part[0] = (double)rr;
   grid_reduce<2>(part, red);
@@ -1377,7 +1643,7 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
     c.npk = (c.np + 15) / 16 * 16;   // tensor-core N and K padding
     c.inv_off = inv_total;           // 16-byte aligned for the bulk copy into shared memory
     inv_total += L.tc ? (long long)c.npk * c.npk : (long long)c.np * c.npp;
-    c.nb = L.tc ? 128 : (L.fdm ? kFdmBatch : class_batch(c.np));
+    c.nb = L.tc ? kTcBatch : (L.fdm ? kFdmBatch : class_batch(c.np));
     L.npmax = std::max(L.npmax, c.np);
     L.gmax = std::max(L.gmax, (long long)c.np * c.nb);
   }
@@ -1600,18 +1866,39 @@ Stencil<float> st_of<float>(const Level& L) { return L.st32; }
 template <>
 Stencil<double> st_of<double>(const Level& L) { return L.st64; }
 
+// r = f - Z_k z on level L (box-sum kernel where the stencil allows it)
+template <typename T, int D>
+void level_residual(const Level& L, const T* f, const T* z, T* r, cudaStream_t s) {
+  if (D == 2 && L.box) {
+    const dim3 grid((unsigned)((L.m + kBoxThreads - 1) / kBoxThreads), (unsigned)((L.m + kBoxSeg - 1) / kBoxSeg));
+    k_residual_box<T><<<grid, kBoxThreads, 0, s>>>((T)L.box_c0, (T)L.box_c1, f, z, r, L.m);
+  } else {
+    k_residual<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(st_of<T>(L), f, z, r, L.m, L.nn);
+  }
+}
+
 template <typename T>
 const T* coarse_S(const Coarse& c);
 template <>
 const float* coarse_S<float>(const Coarse& c) { return c.S32; }
 template <>
 const double* coarse_S<double>(const Coarse& c) { return c.S64; }
+// line-solve tables of the coarsest level in the cycle precision (cyclic
+// reduction beta, gamma on the FFT route; Thomas l, 1/w, e otherwise)
 template <typename T>
-const T* coarse_lam(const Coarse& c);
+void coarse_tri(const Coarse& c, const T** f);
 template <>
-const float* coarse_lam<float>(const Coarse& c) { return c.lam32; }
+void coarse_tri<float>(const Coarse& c, const float** f) {
+  f[0] = c.tri_l32;
+  f[1] = c.tri_w32;
+  f[2] = c.tri_e32;
+}
 template <>
-const double* coarse_lam<double>(const Coarse& c) { return c.lam64; }
+void coarse_tri<double>(const Coarse& c, const double** f) {
+  f[0] = c.tri_l64;
+  f[1] = c.tri_w64;
+  f[2] = c.tri_e64;
+}
 template <typename T>
 const typename cplx<T>::type* coarse_tw(const Coarse& c);
 template <>
@@ -1624,16 +1911,23 @@ int coarse_solve_t(dcg_problem* p, const T* f, T* z, cudaStream_t s) {
   const Coarse& C = p->coarse;
   const long long nn = ipow(C.m, D);
   const int prof = prof_begin(p, PC_COARSE, s, g_capturing);
-  const int nl = fdm_passes<T, D>(f, z, (T*)C.tmp, coarse_S<T>(C), coarse_lam<T>(C), coarse_tw<T>(C), C.log2n2, C.m, s);
+  const T* tri[3];
+  coarse_tri<T>(C, tri);
+  const int nl = fdm_passes<T, D>(f, z, (T*)C.tmp, coarse_S<T>(C), tri[0], tri[1], tri[2], coarse_tw<T>(C), C.log2n2,
+                                  C.m, s);
   note_launches(nl - 1);  // the check below counts one
   DCG_LAUNCH_CHECK();
-  // algorithmic work: dense passes 2 m flops per value and pass; FFT passes
-  // 5 N2 log2(N2) flops per complex transform of length N2 (two lines each)
-  const double flops = C.log2n2 > 0
-                           ? 2.0 * D * ((double)nn / C.m / 2.0) * 5.0 * (double)(1 << C.log2n2) * C.log2n2
-                           : 2.0 * 2 * D * (double)nn * C.m;
-  const double bytes = sizeof(T) * (2.0 * 2 * D * (double)nn + nn) +
-                       (C.log2n2 > 0 ? 0.0 : sizeof(T) * (double)C.m * C.m);
+  // algorithmic work: 2(d-1) transform passes (dense: 2 m flops per value;
+  // FFT: 5 N2 log2(N2) flops per complex transform of length N2, two lines
+  // each) and the line solves (Thomas 4 flops per value, cyclic reduction 5);
+  // bytes: every pass reads and writes the field once, the Thomas sweeps
+  // also read l and 1/w (the cyclic-reduction tables are q values per line)
+  const double npass = 2.0 * (D - 1);
+  const double flops = (C.log2n2 > 0 ? npass * ((double)nn / C.m / 2.0) * 5.0 * (double)(1 << C.log2n2) * C.log2n2 +
+                                           5.0 * (double)nn
+                                     : npass * 2.0 * (double)nn * C.m + 4.0 * (double)nn);
+  const double bytes = sizeof(T) * 2.0 * (npass + 1) * (double)nn +
+                       (C.log2n2 > 0 ? 0.0 : sizeof(T) * ((double)C.m * C.m + 2.0 * (double)nn));
   prof_end(p, prof, s, flops, bytes, g_capturing);
   return DCG_OK;
 }
@@ -1665,9 +1959,7 @@ int ras_step_t(dcg_problem* p, Level& L, cudaStream_t s, bool z_zero = false) {
   const T* rvec = (const T*)L.f;
   if (!z_zero) {
     const int prof = prof_begin(p, PC_TRANSFER, s, g_capturing);
-    k_residual<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(st_of<T>(L), (const T*)L.f, (const T*)L.z, (T*)L.r,
-                                                               L.m, L.nn);
-    DCG_LAUNCH_CHECK();
+    level_residual<T, D>(L, (const T*)L.f, (const T*)L.z, (T*)L.r, s);
     prof_end(p, prof, s, 2.0 * ipow(3, D) * (double)L.nn, sizeof(T) * 3.0 * L.nn, g_capturing);
     rvec = (const T*)L.r;
   }
@@ -1749,9 +2041,7 @@ int wcycle_t(dcg_problem* p, int k, cudaStream_t s, bool z_zero) {
   Level& Lc = p->levels[k - 2];
   for (int i = 0; i < p->opts.m1; ++i) DCG_TRY((ras_step_t<T, D>(p, L, s, z_zero && i == 0)));
   int prof = prof_begin(p, PC_TRANSFER, s, g_capturing);
-  k_residual<T, D><<<grid_for(L.nn, 256, 8192), 256, 0, s>>>(st_of<T>(L), (const T*)L.f, (const T*)L.z, (T*)L.r, L.m,
-                                                             L.nn);
-  DCG_LAUNCH_CHECK();
+  level_residual<T, D>(L, (const T*)L.f, (const T*)L.z, (T*)L.r, s);
   k_restrict<T, D><<<grid_for(Lc.nn, 256, 8192), 256, 0, s>>>((const T*)L.r, (T*)Lc.f, L.m, Lc.m, Lc.nn);
   DCG_LAUNCH_CHECK();
   prof_end(p, prof, s, 2.0 * (ipow(3, D) * (double)L.nn + ipow(3, D) * (double)Lc.nn),
@@ -1815,7 +2105,8 @@ bool exact_mode(const dcg_problem* p) { return p->opts.inner_rule == DCG_INNER_E
 void mg_free(dcg_problem* p) {
   for (auto& L : p->levels) free_level(L);
   p->levels.clear();
-  cudaFree(p->coarse.S64); cudaFree(p->coarse.S32); cudaFree(p->coarse.lam64); cudaFree(p->coarse.lam32);
+  cudaFree(p->coarse.S64); cudaFree(p->coarse.S32); cudaFree(p->coarse.tri_l64); cudaFree(p->coarse.tri_w64); cudaFree(p->coarse.tri_e64);
+  cudaFree(p->coarse.tri_l32); cudaFree(p->coarse.tri_w32); cudaFree(p->coarse.tri_e32);
   cudaFree(p->coarse.tmp);
   cudaFree(p->coarse.tw64); cudaFree(p->coarse.tw32);
   p->coarse = Coarse{};
@@ -1920,8 +2211,28 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
     DCG_CUDA(cudaStreamSynchronize(s));
   }
   cudaFree(scal2);
-  for (auto& L : p->levels)
+  for (auto& L : p->levels) {
     for (int k = 0; k < 27; ++k) L.st32.c[k] = (float)L.st64.c[k];
+    // box-sum form: the 8 neighbour coefficients agree to 1e-12 (they are
+    // equal in exact arithmetic for the Q1 Laplacian; assembly and the
+    // Galerkin products leave rounding), their mean stands for all
+    L.box = false;
+    if (D == 2 && L.m >= 3) {
+      double sum = 0.0, lo = L.st64.c[0], hi = L.st64.c[0];
+      for (int k = 0; k < 9; ++k) {
+        if (k == 4) continue;
+        sum += L.st64.c[k];
+        lo = std::min(lo, L.st64.c[k]);
+        hi = std::max(hi, L.st64.c[k]);
+      }
+      const double c1 = sum / 8.0;
+      if (c1 != 0.0 && hi - lo <= 1e-12 * std::fabs(c1)) {
+        L.box = true;
+        L.box_c1 = c1;
+        L.box_c0 = L.st64.c[4] - c1;
+      }
+    }
+  }
   // coarsest: check the closed form the fast-diagonalisation solver assumes
   {
     Level& L1 = p->levels[0];
@@ -1958,19 +2269,26 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
     C.m = p->levels[0].m;
     const long long nn = p->levels[0].nn;
     DCG_CUDA(cudaMalloc(&C.S64, sizeof(double) * C.m * C.m));
-    DCG_CUDA(cudaMalloc(&C.lam64, sizeof(double) * nn));
+    const long long M1 = nn / C.m;
     DCG_CUDA(cudaMalloc(&C.tmp, tsz * nn));
-    long long work = std::max<long long>((long long)C.m * C.m, nn);
-    int gg = (int)((work + 255) / 256);
-    if (D == 2) k_fdm_setup<2><<<gg, 256, 0, s>>>(C.m, C.S64, C.lam64);
-    else k_fdm_setup<3><<<gg, 256, 0, s>>>(C.m, C.S64, C.lam64);
+    k_fdm_setup<<<grid_for((long long)C.m * C.m, 256), 256, 0, s>>>(C.m, C.S64);
     DCG_LAUNCH_CHECK();
-    // FFT route: m + 1 a power of two, transforms of length 2(m+1) <= 2048
+    // FFT route: m + 1 a power of two, transforms of length 2(m+1) <= 2048,
+    // line solves by cyclic reduction; else dense passes and Thomas sweeps
     C.log2n2 = 0;
+    long long nl_fac = nn, ne_fac = M1;  // sizes of the two factor tables and of e
     if (((C.m + 1) & C.m) == 0 && C.m + 1 <= 1024) {
       int l = 1;
       while ((1 << l) < 2 * (C.m + 1)) ++l;
       C.log2n2 = l;
+      const int q = l - 1;  // m = 2^q - 1
+      nl_fac = (long long)q * M1;
+      ne_fac = 0;
+      DCG_CUDA(cudaMalloc(&C.tri_l64, sizeof(double) * nl_fac));
+      DCG_CUDA(cudaMalloc(&C.tri_w64, sizeof(double) * nl_fac));
+      if (D == 2) k_cr_setup<2><<<grid_for(M1, 128), 128, 0, s>>>(C.m, q, C.tri_l64, C.tri_w64);
+      else k_cr_setup<3><<<grid_for(M1, 128), 128, 0, s>>>(C.m, q, C.tri_l64, C.tri_w64);
+      DCG_LAUNCH_CHECK();
       const int N = C.m + 1;
       std::vector<double2> tw(N);
       std::vector<float2> tw32(N);
@@ -1986,12 +2304,33 @@ int mg_setup(dcg_problem* p, cudaStream_t s) {
       DCG_CUDA(cudaStreamSynchronize(s));  // the host tables go out of scope
       DCG_TRY(set_dst_smem<float>());
       DCG_TRY(set_dst_smem<double>());
+      DCG_CUDA(cudaFuncSetAttribute(k_tri_cr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem));
+      DCG_CUDA(cudaFuncSetAttribute(k_tri_cr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem));
+    } else {
+      if (tri_cols<double>(C.m, M1) < 1) {
+        set_error_msg("coarsest level too large for its line solves (more than 8533 nodes per axis)");
+        return DCG_ERR_UNSUPPORTED;
+      }
+      DCG_CUDA(cudaMalloc(&C.tri_l64, sizeof(double) * nn));
+      DCG_CUDA(cudaMalloc(&C.tri_w64, sizeof(double) * nn));
+      DCG_CUDA(cudaMalloc(&C.tri_e64, sizeof(double) * M1));
+      if (D == 2) k_tri_setup<2><<<grid_for(M1, 128), 128, 0, s>>>(C.m, C.tri_l64, C.tri_w64, C.tri_e64);
+      else k_tri_setup<3><<<grid_for(M1, 128), 128, 0, s>>>(C.m, C.tri_l64, C.tri_w64, C.tri_e64);
+      DCG_LAUNCH_CHECK();
+      DCG_CUDA(cudaFuncSetAttribute(k_tri_last<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem));
+      DCG_CUDA(cudaFuncSetAttribute(k_tri_last<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmem));
     }
     if (fp32) {
       DCG_CUDA(cudaMalloc(&C.S32, sizeof(float) * C.m * C.m));
-      DCG_CUDA(cudaMalloc(&C.lam32, sizeof(float) * nn));
+      DCG_CUDA(cudaMalloc(&C.tri_l32, sizeof(float) * nl_fac));
+      DCG_CUDA(cudaMalloc(&C.tri_w32, sizeof(float) * nl_fac));
       k_to_t<float><<<grid_for(C.m * C.m, 256), 256, 0, s>>>(C.S64, C.S32, (long long)C.m * C.m);
-      k_to_t<float><<<grid_for(nn, 256), 256, 0, s>>>(C.lam64, C.lam32, nn);
+      k_to_t<float><<<grid_for(nl_fac, 256), 256, 0, s>>>(C.tri_l64, C.tri_l32, nl_fac);
+      k_to_t<float><<<grid_for(nl_fac, 256), 256, 0, s>>>(C.tri_w64, C.tri_w32, nl_fac);
+      if (ne_fac > 0) {
+        DCG_CUDA(cudaMalloc(&C.tri_e32, sizeof(float) * ne_fac));
+        k_to_t<float><<<grid_for(ne_fac, 256), 256, 0, s>>>(C.tri_e64, C.tri_e32, ne_fac);
+      }
       DCG_LAUNCH_CHECK();
     }
   }
@@ -2044,7 +2383,11 @@ int inner_residual(dcg_problem* p, const double* g, const double* z, cudaStream_
   const int grid = grid_for(L.nn, 256, kRedGrid);
   Reduce red = make_reduce(p, S_TMP0);  // S_TMP0 <- ||r||^2, S_TMP1 <- ||g||^2
   const int prof = prof_begin(p, PC_INNER_RES, s);
-  if (p->dim == 2)
+  const int gx = (L.m + kBoxThreads - 1) / kBoxThreads, gy = (L.m + kBoxSeg - 1) / kBoxSeg;
+  if (p->dim == 2 && L.box && (long long)gx * gy <= kMaxRedCtas)
+    k_inner_residual_box<T><<<gx * gy, kBoxThreads, 0, s>>>(L.box_c0, L.box_c1, g, z, (T*)L.f, (T*)L.z, L.m, gx, red,
+                                                            with_g);
+  else if (p->dim == 2)
     k_inner_residual<T, 2><<<grid, 256, 0, s>>>(L.st64, g, z, (T*)L.f, (T*)L.z, nullptr, L.m, L.nn, red, with_g);
   else
     k_inner_residual<T, 3><<<grid, 256, 0, s>>>(L.st64, g, z, (T*)L.f, (T*)L.z, nullptr, L.m, L.nn, red, with_g);
@@ -2240,8 +2583,10 @@ extern "C" int dcg_coarse_solve_static(dcg_problem* p, const double* f_dev, doub
     g_static_coarse_ptr[dev].store(tmp, std::memory_order_release);  // every thread finds the same address
   }
   cudaStream_t s = (cudaStream_t)stream;
-  const int nl = D == 2 ? fdm_passes<double, 2>(f_dev, z_dev, tmp, C.S64, C.lam64, C.tw64, C.log2n2, C.m, s)
-                        : fdm_passes<double, 3>(f_dev, z_dev, tmp, C.S64, C.lam64, C.tw64, C.log2n2, C.m, s);
+  const int nl = D == 2 ? fdm_passes<double, 2>(f_dev, z_dev, tmp, C.S64, C.tri_l64, C.tri_w64, C.tri_e64, C.tw64,
+                                                C.log2n2, C.m, s)
+                        : fdm_passes<double, 3>(f_dev, z_dev, tmp, C.S64, C.tri_l64, C.tri_w64, C.tri_e64, C.tw64,
+                                                C.log2n2, C.m, s);
   note_launches(nl - 1);
   DCG_LAUNCH_CHECK();
   return DCG_OK;

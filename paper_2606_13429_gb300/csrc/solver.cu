@@ -37,6 +37,10 @@ enum Rule { R_CG = 0, R_FCG1 = 1, R_FR = 2, R_FCGINF = 3, R_GMRES = 4 };
 
 // x += a d; r -= a q; reduces (r.r, r.q) into (S_RRN, S_RQ);
 // a = (FCG ? d.r : r.r) / d.q, zero when d.q <= 0 (breakdown: the host stops).
+// V2: all four vectors 16-byte aligned; a thread takes element pairs
+// (16-byte accesses, two independent partial sums per value), and the last
+// element of an odd n is done by thread 0 of CTA 0.
+template <bool V2>
 __global__ void k_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ d,
                          const double* __restrict__ q, long long n, const double* __restrict__ sc, int use_dr,
                          Reduce red) {
@@ -44,7 +48,30 @@ __global__ void k_update(double* __restrict__ x, double* __restrict__ r, const d
   const double num = use_dr ? sc[S_DR] : sc[S_RR];
   const double a = (dq > 0.0) ? num / dq : 0.0;
   double part[2] = {0.0, 0.0};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  long long i0 = tid;
+  if (V2) {
+    double p0b = 0.0, p1b = 0.0;
+    const long long n2 = n >> 1;
+    for (long long i = tid; i < n2; i += stride) {
+      const double2 di = reinterpret_cast<const double2*>(d)[i], qi = reinterpret_cast<const double2*>(q)[i];
+      double2 xi = reinterpret_cast<double2*>(x)[i], ri = reinterpret_cast<double2*>(r)[i];
+      xi.x = fma(a, di.x, xi.x);
+      xi.y = fma(a, di.y, xi.y);
+      ri.x = fma(-a, qi.x, ri.x);
+      ri.y = fma(-a, qi.y, ri.y);
+      reinterpret_cast<double2*>(x)[i] = xi;
+      reinterpret_cast<double2*>(r)[i] = ri;
+      part[0] = fma(ri.x, ri.x, part[0]);
+      p0b = fma(ri.y, ri.y, p0b);
+      part[1] = fma(ri.x, qi.x, part[1]);
+      p1b = fma(ri.y, qi.y, p1b);
+    }
+    part[0] += p0b;
+    part[1] += p1b;
+    i0 = (n & 1) && tid == 0 ? n - 1 : n;  // the odd tail, if any
+  }
+  for (long long i = i0; i < n; i += (V2 ? n : stride)) {
     const double di = d[i], qi = q[i];
     x[i] = fma(a, di, x[i]);
     const double ri = fma(-a, qi, r[i]);
@@ -61,13 +88,32 @@ __global__ void k_update(double* __restrict__ x, double* __restrict__ r, const d
 // then d.r -> S_DR and S_RR <- rr_new
 // stop (device flag, may be null): the loop of a captured solve has ended and
 // the next direction is not needed (uniform early exit of every CTA)
+// V2 as in k_update
+template <bool V2>
 __global__ void k_direction(double* __restrict__ d, const double* __restrict__ r, long long n, double* __restrict__ sc,
                             int fcg, Reduce red, const int* __restrict__ stop) {
   if (stop && *stop) return;
   const double rrn = sc[S_RRN];  // r.r of the new residual (written by k_update)
   const double beta = fcg ? -(sc[S_RQ] / sc[S_DQ]) : rrn / sc[S_RR];
   double part[1] = {0.0};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  long long i0 = tid;
+  if (V2) {
+    double pb = 0.0;
+    const long long n2 = n >> 1;
+    for (long long i = tid; i < n2; i += stride) {
+      const double2 ri = reinterpret_cast<const double2*>(r)[i];
+      double2 di = reinterpret_cast<double2*>(d)[i];
+      di.x = fma(beta, di.x, ri.x);
+      di.y = fma(beta, di.y, ri.y);
+      reinterpret_cast<double2*>(d)[i] = di;
+      part[0] = fma(di.x, ri.x, part[0]);
+      pb = fma(di.y, ri.y, pb);
+    }
+    part[0] += pb;
+    i0 = (n & 1) && tid == 0 ? n - 1 : n;
+  }
+  for (long long i = i0; i < n; i += (V2 ? n : stride)) {
     const double ri = r[i];
     const double di = fma(beta, d[i], ri);
     d[i] = di;
@@ -608,7 +654,10 @@ int solver_update(dcg_problem* p, double* x, double* r, const double* d, const d
                   cudaStream_t s) {
   const long long N = p->N;
   const int prof = prof_begin(p, PC_VEC, s);
-  k_update<<<grid_n(N), kRedThreads, 0, s>>>(x, r, d, q, N, p->scal, use_dr, make_reduce(p, S_RRN));
+  if (aligned16(x) && aligned16(r) && aligned16(d) && aligned16(q))
+    k_update<true><<<grid_n(N), kRedThreads, 0, s>>>(x, r, d, q, N, p->scal, use_dr, make_reduce(p, S_RRN));
+  else
+    k_update<false><<<grid_n(N), kRedThreads, 0, s>>>(x, r, d, q, N, p->scal, use_dr, make_reduce(p, S_RRN));
   DCG_LAUNCH_CHECK();
   prof_end(p, prof, s, 8.0 * N, 48.0 * N);
   return DCG_OK;
@@ -617,7 +666,10 @@ int solver_update(dcg_problem* p, double* x, double* r, const double* d, const d
 int solver_direction(dcg_problem* p, double* d, const double* r, int fcg, cudaStream_t s, const int* stop) {
   const long long N = p->N;
   const int prof = prof_begin(p, PC_VEC, s);
-  k_direction<<<grid_n(N), kRedThreads, 0, s>>>(d, r, N, p->scal, fcg, make_reduce(p, S_DR), stop);
+  if (aligned16(d) && aligned16(r))
+    k_direction<true><<<grid_n(N), kRedThreads, 0, s>>>(d, r, N, p->scal, fcg, make_reduce(p, S_DR), stop);
+  else
+    k_direction<false><<<grid_n(N), kRedThreads, 0, s>>>(d, r, N, p->scal, fcg, make_reduce(p, S_DR), stop);
   DCG_LAUNCH_CHECK();
   prof_end(p, prof, s, 4.0 * N, 24.0 * N);
   k_roll<<<1, 1, 0, s>>>(p->scal, stop);

@@ -418,17 +418,88 @@ __global__ void k_q_from_t(const double* __restrict__ t, const double* __restric
   grid_reduce<1>(part, red);
 }
 
+// 2D: the same product in separable form. The stencils of div_stencil are
+// products of 1D factors: G[x][x] = K1 (x) M1, G[y][y] = M1 (x) K1 and
+// G[x][y] = G[y][x] = (+-1/2 first differences along both axes), h cancelling
+// in 2D. With the row quantities of column x at row y'
+//   u = z(x-1) + z(x+1),  kx = 2 z(x) - u,  mx = 4 z(x) + u,  cx = z(x+1) - z(x-1)
+// the three distinct products at row y are
+//   G_xx zh = (kx(y-1) + kx(y+1) + 4 kx(y)) / 6
+//   G_yy zh = (2 mx(y) - mx(y-1) - mx(y+1)) / 6
+//   G_xy zh = (cx(y-1) - cx(y+1)) / 4,
+// computed with row quantities that slide along y: 17 FP64 operations per
+// node (with the four updates and the dot product) instead of 34. A thread
+// walks kQSeg rows of one column (consecutive threads, consecutive columns);
+// the 1D grid holds column blocks x row segments for the grid reduction.
+constexpr int kQSeg = 16, kQThreads = 128;
+
+__global__ void __launch_bounds__(kQThreads) k_q_from_t_2d(const double* __restrict__ t, const double* __restrict__ zh,
+                                                           const double* __restrict__ dv, double* __restrict__ q,
+                                                           int m, int gx, double isd, Reduce red) {
+  double part[1] = {0.0};
+  const int bx = blockIdx.x % gx, by = blockIdx.x / gx;
+  const int x = bx * kQThreads + threadIdx.x;
+  if (x < m) {
+    auto rowq = [&](int y, double& kx, double& mx, double& cx) {
+      kx = mx = cx = 0.0;
+      if (y < 0 || y >= m) return;
+      const double* r = zh + (long long)m * y;
+      const double zc = __ldg(r + x);
+      const double zl = x > 0 ? __ldg(r + x - 1) : 0.0;
+      const double zr = x + 1 < m ? __ldg(r + x + 1) : 0.0;
+      const double u = zl + zr;
+      kx = fma(2.0, zc, -u);
+      mx = fma(4.0, zc, u);
+      cx = zr - zl;
+    };
+    const double axx = isd / 6.0, axy = isd / 4.0;
+    const int y0 = by * kQSeg, y1 = min(y0 + kQSeg, m);
+    double km, mm, cm, k0, m0, c0;
+    rowq(y0 - 1, km, mm, cm);
+    rowq(y0, k0, m0, c0);
+    for (int y = y0; y < y1; ++y) {
+      double kp, mp, cp;
+      rowq(y + 1, kp, mp, cp);
+      const double gxx = fma(4.0, k0, km + kp);
+      const double gyy = fma(2.0, m0, -(mm + mp));
+      const double gxy = cm - cp;
+      const long long a = x + (long long)m * y;
+      const double2* t2 = reinterpret_cast<const double2*>(t + 4 * a);
+      const double2* d2 = reinterpret_cast<const double2*>(dv + 4 * a);
+      const double2 ta = __ldg(t2), tb = __ldg(t2 + 1), da = __ldg(d2), db = __ldg(d2 + 1);
+      // components (k, p) = xx, xy, yx, yy
+      const double q0 = fma(-axx, gxx, ta.x), q1 = fma(-axy, gxy, ta.y);
+      const double q2 = fma(-axy, gxy, tb.x), q3 = fma(-axx, gyy, tb.y);
+      double2* o2 = reinterpret_cast<double2*>(q + 4 * a);
+      o2[0] = make_double2(q0, q1);
+      o2[1] = make_double2(q2, q3);
+      part[0] = fma(da.x, q0, part[0]);
+      part[0] = fma(da.y, q1, part[0]);
+      part[0] = fma(db.x, q2, part[0]);
+      part[0] = fma(db.y, q3, part[0]);
+      km = k0; mm = m0; cm = c0;
+      k0 = kp; m0 = mp; c0 = cp;
+    }
+  }
+  grid_reduce<1>(part, red);
+}
+
 }  // namespace
 
 int q_from_t(dcg_problem* p, const double* t, const double* zh, const double* dv, double* q, int slot,
              cudaStream_t s) {
-  DivStencil G;
-  div_stencil(p->dim, p->n, G.c);
   const double isd = 1.0 / std::sqrt((double)p->dim);
-  const int g = grid_for(p->n_nodes, 256, kRedGrid);
   const int prof = prof_begin(p, PC_VEC, s);
-  if (p->dim == 2) k_q_from_t<2><<<g, 256, 0, s>>>(t, zh, dv, q, G, p->m, p->n_nodes, isd, make_reduce(p, slot));
-  else k_q_from_t<3><<<g, 256, 0, s>>>(t, zh, dv, q, G, p->m, p->n_nodes, isd, make_reduce(p, slot));
+  const int gx = (p->m + kQThreads - 1) / kQThreads, gy = (p->m + kQSeg - 1) / kQSeg;
+  if (p->dim == 2 && (long long)gx * gy <= kMaxRedCtas) {
+    k_q_from_t_2d<<<gx * gy, kQThreads, 0, s>>>(t, zh, dv, q, p->m, gx, isd, make_reduce(p, slot));
+  } else {
+    DivStencil G;
+    div_stencil(p->dim, p->n, G.c);
+    const int g = grid_for(p->n_nodes, 256, kRedGrid);
+    if (p->dim == 2) k_q_from_t<2><<<g, 256, 0, s>>>(t, zh, dv, q, G, p->m, p->n_nodes, isd, make_reduce(p, slot));
+    else k_q_from_t<3><<<g, 256, 0, s>>>(t, zh, dv, q, G, p->m, p->n_nodes, isd, make_reduce(p, slot));
+  }
   DCG_LAUNCH_CHECK();
   prof_end(p, prof, s, 2.0 * p->N * (p->dim == 2 ? 6.5 : 15.0), 8.0 * (3.0 * p->N + p->n_nodes));
   return DCG_OK;

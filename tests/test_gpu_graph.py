@@ -131,17 +131,19 @@ def test_graph_launch_counts_reported():
     assert counts[1] <= 2 * counts[0]
 
 
-def test_batched_graph_equals_sequential_and_oracle():
+@pytest.mark.parametrize("loop", [0, 1])
+def test_batched_graph_equals_sequential_and_oracle(loop):
     """A batch of 2D and 3D problems (several sizes, dt, precisions), 3
-    right-hand sides each, captured into one graph: bitwise equal to solving
-    the pairs one by one, and the FP64 pairs equal to the oracle's."""
+    right-hand sides each, driven by host workers (device_loop = 0) or
+    captured into one graph (device_loop = 1): bitwise equal to solving the
+    pairs one by one, and the FP64 pairs equal to the oracle's."""
     specs = [(2, 16, 1e-6, dcg.DCG_FP64), (2, 24, 1e-4, dcg.DCG_MIXED), (3, 8, 1e-4, dcg.DCG_FP64),
              (2, 40, 1e-2, dcg.DCG_FP64), (3, 12, 1e-5, dcg.DCG_MIXED)]
     nrhs = 3
     probs, fs = [], []
     for p, (d, n, dt, prec) in enumerate(specs):
         prob = dcg.dcg_assemble(d, n, dt)
-        dcg.dcg_setup(prob, dcg.options(precision=prec, stall_window=0))
+        dcg.dcg_setup(prob, dcg.options(precision=prec, stall_window=0, device_loop=loop))
         probs.append(prob)
         for r in range(nrhs):
             fs.append(dev(inputs.rhs(7, prob.N, p=p, r=r)))

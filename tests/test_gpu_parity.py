@@ -353,6 +353,8 @@ def test_edge_cases():
         dcg.dcg_setup(prob, dcg.options(overlap=9, patch=4))
     with pytest.raises(dcg.DCGError):
         dcg.dcg_setup(prob, dcg.options(patch=16, overlap=1))
+    with pytest.raises(dcg.DCGError):
+        dcg.dcg_setup(prob, dcg.options(device_loop=2))
 
 
 @pytest.mark.parametrize("n", [2, 3, 4, 5])
