@@ -200,6 +200,101 @@ __global__ void k_spmv(SpmvArgs A) {
 }
 
 
+// 3D (9 x 9 blocks), entry-parallel: a CTA of 256 threads takes 7 block
+// rows at a time; thread t < 231 owns the structural nonzero number t % 33
+// (Section 3.1: 33 of the 81 entries of a block) of every block of block
+// row t / 33 and walks that row's blocks. The 33 threads of a block row read
+// their entries of each block's 648 contiguous bytes together, the 48
+// structural zeros are neither read nor multiplied, and x[col * 9 + c] is
+// shared by the threads of column c. A row's partial sums are added in
+// shared memory in the order of its entries (deterministic).
+__host__ __device__ constexpr bool nz3(int r, int c) {
+  // row r = (k, i) = (r / 3, r % 3): diagonal rows (k == i) couple the
+  // diagonal components l*3+l and the components k*3+q; the others only k*3+q
+  return (r / 3 == r % 3) ? (c % 4 == 0 || c / 3 == r / 3) : (c / 3 == r / 3);
+}
+// the nonzeros r*9 + c in row-major order, and where each row starts (the
+// lists are checked against nz3 at compile time)
+#define DCG_NZ3_RC 0, 1, 2, 4, 8, 9, 10, 11, 18, 19, 20, 30, 31, 32, 36, 39, 40, 41, 44, 48, 49, 50, 60, 61, 62, \
+                   69, 70, 71, 72, 76, 78, 79, 80
+#define DCG_NZ3_ROW 0, 5, 8, 11, 14, 19, 22, 25, 28, 33
+constexpr int kNz3 = 33, kRows3 = 7;
+constexpr unsigned char kNz3Rc[kNz3] = {DCG_NZ3_RC};
+constexpr unsigned char kNz3Row[10] = {DCG_NZ3_ROW};
+constexpr bool nz3_tables_ok() {
+  int e = 0;
+  for (int r = 0; r < 9; ++r) {
+    if (kNz3Row[r] != e) return false;
+    for (int c = 0; c < 9; ++c)
+      if (nz3(r, c)) {
+        if (e >= kNz3 || kNz3Rc[e] != r * 9 + c) return false;
+        ++e;
+      }
+  }
+  return e == kNz3 && kNz3Row[9] == kNz3;
+}
+static_assert(nz3_tables_ok(), "3D block nonzero tables");
+__constant__ unsigned char c_nz3_rc[kNz3] = {DCG_NZ3_RC};
+__constant__ unsigned char c_nz3_row[10] = {DCG_NZ3_ROW};
+
+template <int XM, int OM, bool DOT>
+__global__ void __launch_bounds__(256) k_spmv3(SpmvArgs A) {
+  constexpr int B = 9;
+  __shared__ double s_part[kRows3][kNz3];
+  __shared__ double s_out[kRows3][9];
+  const int t = threadIdx.x;
+  const int lb = t / kNz3, e = t - lb * kNz3;
+  const int rc = t < kRows3 * kNz3 ? c_nz3_rc[e] : 0, r = rc / 9, c = rc - r * 9;
+  const bool act = t < kRows3 * kNz3 && (OM != OM_VT || r % 4 == 0);
+  double part[1] = {0.0};
+  for (long long base = (long long)blockIdx.x * kRows3; base < A.n_nodes; base += (long long)gridDim.x * kRows3) {
+    const long long a = base + lb;
+    double acc = 0.0;
+    if (act && a < A.n_nodes) {
+      const int j0 = __ldg(A.row_ptr + a), j1 = __ldg(A.row_ptr + a + 1);
+#pragma unroll 4
+      for (int j = j0; j < j1; ++j) {
+        const long long col = __ldg(A.col_idx + j);
+        acc = fma(__ldg(A.vals + (long long)j * 81 + rc), xval<3, XM>(A, col, c), acc);
+      }
+    }
+    if (t < kRows3 * kNz3) s_part[lb][e] = acc;
+    __syncthreads();
+    if (t < kRows3 * 9) {
+      const int b2 = t / 9, r2 = t - b2 * 9;
+      const long long a2 = base + b2;
+      const int e0 = c_nz3_row[r2], e1 = c_nz3_row[r2 + 1];
+      double sum = s_part[b2][e0];
+      for (int k = e0 + 1; k < e1; ++k) sum += s_part[b2][k];
+      if (a2 < A.n_nodes) {
+        const long long row = a2 * B + r2;
+        if (OM == OM_Y) {
+          A.y[row] = sum;
+          if (DOT) part[0] = fma(A.dvec[row], sum, part[0]);
+        } else if (OM == OM_FMY) {
+          const double out = __dsub_rn(A.f[row], sum);
+          A.y[row] = out;
+          if (DOT) part[0] = fma(out, out, part[0]);
+        } else if (OM == OM_YVT) {
+          A.y[row] = sum;
+        }
+      }
+      s_out[b2][r2] = sum;
+    }
+    if (OM == OM_VT || OM == OM_YVT) {
+      __syncthreads();
+      if (t < kRows3 && base + t < A.n_nodes) {
+        const double g = (s_out[t][0] + s_out[t][4] + s_out[t][8]) * A.isd;
+        if (OM == OM_VT) A.y[base + t] = g;
+        else A.g[base + t] = g;
+        if (DOT) part[0] = fma(g, g, part[0]);
+      }
+    }
+    __syncthreads();
+  }
+  if (DOT) grid_reduce<1>(part, A.red);
+}
+
 // w = x - V zh (node-major, the d diagonal components of each node shifted):
 // formed once per node instead of once per stored block that reads it, which
 // keeps the FP64 arithmetic of the deflated product at that of A x
@@ -241,8 +336,8 @@ int launch(dcg_problem* p, SpmvArgs a, cudaStream_t s, bool lowp = false) {
     const int threads = 32 * (OM == OM_VT ? 2 : 4);
     k_spmv<2, XM, OM, DOT><<<grid, threads, 0, s>>>(a);
   } else {
-    const int threads = 32 * (OM == OM_VT ? 3 : 9);
-    k_spmv<3, XM, OM, DOT><<<grid, threads, 0, s>>>(a);
+    const int grid3 = grid_for((p->n_nodes + kRows3 - 1) / kRows3, 1, DOT ? 2 * kRedGrid : kMaxRedCtas);
+    k_spmv3<XM, OM, DOT><<<grid3, 256, 0, s>>>(a);
   }
   DCG_LAUNCH_CHECK();
   prof_end(p, prof, s, 2.0 * fma_blk * nnzb, bytes);
