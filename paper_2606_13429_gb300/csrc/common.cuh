@@ -65,10 +65,37 @@ constexpr int kMaxRedCtas = 65536;
 // is amortised
 constexpr int kRedGrid = 8 * 152;
 
+// Block-wide sums of NV doubles per thread, left in thread 0. This GPU
+// issues FP64 at 2 lanes per clock per SM, so a warp-wide FP64 add costs 16
+// SM clocks whatever its lanes do. Blocks of up to kRedTree threads (whole
+// warps) therefore stage their partials in shared memory, warp 0 adds the
+// nwarp values of each lane (nwarp - 1 FP64 warp instructions per value) and
+// folds its 32 lanes (5 more): 12 instructions per value for 256 threads,
+// against 45 for a shuffle tree in every warp. Fixed order: deterministic.
+constexpr int kRedTree = 256;
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /*[32*NV]*/) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarp = (blockDim.x + 31) >> 5;
+  if (blockDim.x <= kRedTree && (blockDim.x & 31) == 0) {
+    __shared__ double stage[kRedTree * NV];
+    const int bd = blockDim.x;
+    __syncthreads();  // a previous call's readers are done with the stage
+#pragma unroll
+    for (int k = 0; k < NV; ++k) stage[k * bd + threadIdx.x] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        double x = stage[k * bd + lane];
+        for (int w = 1; w < nwarp; ++w) x += stage[k * bd + w * 32 + lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        v[k] = x;
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     double x = v[k];

@@ -379,7 +379,7 @@ __global__ void k_residual(Stencil<T> st, const T* __restrict__ f, const T* __re
 // spends). A thread walks kBoxSeg rows of one column; consecutive threads
 // take consecutive columns, so every row access is coalesced. Entries
 // outside the grid are zero (Dirichlet nodes eliminated).
-constexpr int kBoxSeg = 16;
+constexpr int kBoxSeg = 8;
 constexpr int kBoxThreads = 128;
 
 template <typename T>
@@ -395,7 +395,9 @@ __device__ __forceinline__ T box_row(const T* __restrict__ z, int x, int y, int 
 }
 
 // Walks rows y0 .. y0 + kBoxSeg - 1 of column x and calls
-// body(a, r_a) with r_a = f_a - (Z z)_a.
+// body(a, r_a) with r_a = f_a - (Z z)_a. Rows are loaded kBoxU at a time
+// (all their loads in flight together) before the sums slide over them.
+constexpr int kBoxU = 4;
 template <typename T, typename F, typename Body>
 __device__ __forceinline__ void box_residual_walk(T c0, T c1, const F* __restrict__ f, const T* __restrict__ z, int m,
                                                   int x, int y0, Body&& body) {
@@ -403,16 +405,23 @@ __device__ __forceinline__ void box_residual_walk(T c0, T c1, const F* __restric
   T cm, c0v;
   T sm = box_row(z, x, y0 - 1, m, cm);
   T s0 = box_row(z, x, y0, m, c0v);
-  for (int y = y0; y < y1; ++y) {
-    T cp;
-    const T sp = box_row(z, x, y + 1, m, cp);
-    const long long a = x + (long long)m * y;
-    const T box = (sm + s0) + sp;
-    const T r = fma(-c1, box, fma(-c0, c0v, (T)__ldg(f + a)));
-    body(a, r);
-    sm = s0;
-    s0 = sp;
-    c0v = cp;
+  for (int y = y0; y < y1; y += kBoxU) {
+    T sp[kBoxU], cp[kBoxU], fv[kBoxU];
+#pragma unroll
+    for (int u = 0; u < kBoxU; ++u) {
+      sp[u] = box_row(z, x, y + u + 1, m, cp[u]);
+      fv[u] = y + u < y1 ? (T)__ldg(f + x + (long long)m * (y + u)) : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < kBoxU; ++u) {
+      if (y + u < y1) {
+        const T box = (sm + s0) + sp[u];
+        body(x + (long long)m * (y + u), fma(-c1, box, fma(-c0, c0v, fv[u])));
+      }
+      sm = s0;
+      s0 = sp[u];
+      c0v = cp[u];
+    }
   }
 }
 
@@ -792,8 +801,8 @@ __global__ void __launch_bounds__(256) k_ras_solve_tc(RasArgs ra, const float* _
 // A CTA takes one work item (boxes of one class); every phase gives each
 // thread one grid line of one box (box index fastest), the box values live
 // in shared memory with an odd row stride (np + 1), lines in registers (LM
-// = the largest extent, a compile-time bound). Results are written in the
-// work item's layout y[item][i][nb] that k_ras_update reads.
+// = the largest extent, a compile-time bound). Results are written box-major,
+// y[item][b][i], the layout the level's index table gives k_ras_update.
 // S applied along one grid line of length l (entries base + x * stride),
 // in place. Row j of the sine matrix is symmetric (j even) or antisymmetric
 // (j odd) about the line's midpoint, so the line is folded once into
@@ -871,7 +880,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_ras_fdm(RasArgs ra, const doubl
   const int cls = ra.work[3 * w], first = ra.work[3 * w + 1], cnt = ra.work[3 * w + 2];
   const RasClass C = ra.classes[cls];
   const int lx = C.len[0], ly = C.len[1], lz = D > 2 ? C.len[2] : 1;
-  const int np = C.np, ld = np + 1, NB = C.nb;
+  const int np = C.np, ld = np + 1;
   const int tid = threadIdx.x, nt = blockDim.x;
   // gather the residual on the boxes
   for (int t = tid; t < cnt * np; t += nt) {
@@ -911,11 +920,18 @@ __global__ void __launch_bounds__(kFdmThreads) k_ras_fdm(RasArgs ra, const doubl
     }
     __syncthreads();
   }
-  // back along x, results to the work item's layout (box index fastest)
-  double* yi = y + ra.item_off[w];
+  // back along x in place, then the results to the work item's box-major
+  // layout y[item][b][i] with consecutive threads on consecutive entries
+  // (the per-node weighted sum then reads runs of neighbouring nodes)
   for (int t = tid; t < cnt * ly * lz; t += nt) {
     const int b = t % cnt, line = t / cnt;
-    fdm_line_transform<LM>(W, b * ld + line * lx, 1, lx, Sx, yi + (size_t)line * lx * NB + b, NB);
+    fdm_line_transform<LM>(W, b * ld + line * lx, 1, lx, Sx);
+  }
+  __syncthreads();
+  double* yi = y + ra.item_off[w];
+  for (int t = tid; t < cnt * np; t += nt) {
+    const int b = t / np, i = t - b * np;
+    yi[t] = W[b * ld + i];
   }
 }
 
@@ -1719,7 +1735,10 @@ int setup_ras(dcg_problem* p, Level& L, bool fp32, cudaStream_t s) {
           if (l3[k] < lo || l3[k] >= hi) slot |= 1 << k;
         }
         const long long node = o4.w + (long long)local_node[c.local_off + i];
-        ysrc[(size_t)node * SL + slot] = (int)(item_off[w] + (long long)i * c.nb + b);
+        // item layout: [i][b] (entry-major) for the product kernels, [b][i]
+        // (box-major) for the fast-diagonalisation kernel
+        const long long at = L.fdm ? (long long)b * c.np + i : (long long)i * c.nb + b;
+        ysrc[(size_t)node * SL + slot] = (int)(item_off[w] + at);
       }
     }
   }

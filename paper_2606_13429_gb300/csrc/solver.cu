@@ -44,9 +44,16 @@ template <bool V2>
 __global__ void k_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ d,
                          const double* __restrict__ q, long long n, const double* __restrict__ sc, int use_dr,
                          Reduce red) {
-  const double dq = sc[S_DQ];
-  const double num = use_dr ? sc[S_DR] : sc[S_RR];
-  const double a = (dq > 0.0) ? num / dq : 0.0;
+  // one FP64 division per CTA, not per thread (a division is a sequence of
+  // FP64 operations, as costly here as a thread's share of the update)
+  __shared__ double s_a;
+  if (threadIdx.x == 0) {
+    const double dq = sc[S_DQ];
+    const double num = use_dr ? sc[S_DR] : sc[S_RR];
+    s_a = (dq > 0.0) ? num / dq : 0.0;
+  }
+  __syncthreads();
+  const double a = s_a;
   double part[2] = {0.0, 0.0};
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
   long long i0 = tid;
@@ -93,8 +100,13 @@ template <bool V2>
 __global__ void k_direction(double* __restrict__ d, const double* __restrict__ r, long long n, double* __restrict__ sc,
                             int fcg, Reduce red, const int* __restrict__ stop) {
   if (stop && *stop) return;
-  const double rrn = sc[S_RRN];  // r.r of the new residual (written by k_update)
-  const double beta = fcg ? -(sc[S_RQ] / sc[S_DQ]) : rrn / sc[S_RR];
+  __shared__ double s_beta;
+  if (threadIdx.x == 0) {
+    const double rrn = sc[S_RRN];  // r.r of the new residual (written by k_update)
+    s_beta = fcg ? -(sc[S_RQ] / sc[S_DQ]) : rrn / sc[S_RR];
+  }
+  __syncthreads();
+  const double beta = s_beta;
   double part[1] = {0.0};
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
   long long i0 = tid;
@@ -190,9 +202,12 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_dot(const double* __restr
   }
 }
 
-// coef[j] = sum over CTAs of part[j][.] (one CTA per window entry)
+// coef[j] = (sum over CTAs of part[j][.]) / (d_k, q_k), k = first + j: the
+// coefficient of d_k in the orthogonalisation (one CTA per window entry, so
+// one division per coefficient)
 __global__ void k_multi_dot_finish(const double* __restrict__ part, int nbx, const int* __restrict__ ndir, int cap,
-                                   double* __restrict__ coef, const int* __restrict__ stop) {
+                                   const double* __restrict__ dqs, double* __restrict__ coef,
+                                   const int* __restrict__ stop) {
   __shared__ double smem[32];
   if (stop && *stop) return;
   const int K = fcg_window(ndir[0], cap);
@@ -201,12 +216,12 @@ __global__ void k_multi_dot_finish(const double* __restrict__ part, int nbx, con
   double v[1] = {0.0};
   for (int b = threadIdx.x; b < nbx; b += blockDim.x) v[0] += part[(size_t)j * nbx + b];
   block_sum<1>(v, smem);
-  if (threadIdx.x == 0) coef[j] = v[0];
+  if (threadIdx.x == 0) coef[j] = v[0] / dqs[(ndir[0] - K + j) % cap];
 }
 
-// d_i = r - sum_j (c_j / dq_{first+j}) d_{first+j}; (d_i, r) -> red
+// d_i = r - sum_j coef_j d_{first+j} (coef_j = c_j / dq_{first+j}); (d_i, r) -> red
 __global__ void k_orth_direction(double* __restrict__ d, const double* __restrict__ r, const double* __restrict__ dirs,
-                                 const double* __restrict__ coef, const double* __restrict__ dqs,
+                                 const double* __restrict__ coef,
                                  const int* __restrict__ ndir, int cap, long long n, Reduce red,
                                  const int* __restrict__ stop) {
   if (stop && *stop) return;
@@ -218,7 +233,7 @@ __global__ void k_orth_direction(double* __restrict__ d, const double* __restric
     double dt = rt;
     for (int j = 0; j < K; ++j) {
       const int sl = (first + j) % cap;
-      dt = fma(-(coef[j] / dqs[sl]), dirs[(size_t)sl * n + t], dt);
+      dt = fma(-coef[j], dirs[(size_t)sl * n + t], dt);
     }
     d[t] = dt;
     part[0] = fma(dt, rt, part[0]);
@@ -699,9 +714,10 @@ int solver_fcg_direction(dcg_problem* p, cudaStream_t s, const int* stop, int K,
   const int prof = prof_begin(p, PC_VEC, s);
   k_multi_dot<<<dim3(kMultiDotGrid, gy), kRedThreads, 0, s>>>(b.r, b.qdirs, b.ndir_dev, b.ndir_cap, N, b.part, stop);
   DCG_LAUNCH_CHECK();
-  k_multi_dot_finish<<<finish_grid, kRedThreads, 0, s>>>(b.part, kMultiDotGrid, b.ndir_dev, b.ndir_cap, b.coef, stop);
+  k_multi_dot_finish<<<finish_grid, kRedThreads, 0, s>>>(b.part, kMultiDotGrid, b.ndir_dev, b.ndir_cap, b.dqs, b.coef,
+                                                         stop);
   DCG_LAUNCH_CHECK();
-  k_orth_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, b.dirs, b.coef, b.dqs, b.ndir_dev, b.ndir_cap, N,
+  k_orth_direction<<<grid_n(N), kRedThreads, 0, s>>>(b.d, b.r, b.dirs, b.coef, b.ndir_dev, b.ndir_cap, N,
                                                       make_reduce(p, S_DR), stop);
   DCG_LAUNCH_CHECK();
   prof_end(p, prof, s, 4.0 * K * N, 8.0 * N * (2.0 * K + 2.0 + (double)gy));

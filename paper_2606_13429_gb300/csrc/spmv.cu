@@ -526,7 +526,7 @@ __global__ void k_q_from_t(const double* __restrict__ t, const double* __restric
 // node (with the four updates and the dot product) instead of 34. A thread
 // walks kQSeg rows of one column (consecutive threads, consecutive columns);
 // the 1D grid holds column blocks x row segments for the grid reduction.
-constexpr int kQSeg = 16, kQThreads = 128;
+constexpr int kQSeg = 16, kQThreads = 128, kQU = 2;
 
 __global__ void __launch_bounds__(kQThreads) k_q_from_t_2d(const double* __restrict__ t, const double* __restrict__ zh,
                                                            const double* __restrict__ dv, double* __restrict__ q,
@@ -552,28 +552,45 @@ __global__ void __launch_bounds__(kQThreads) k_q_from_t_2d(const double* __restr
     double km, mm, cm, k0, m0, c0;
     rowq(y0 - 1, km, mm, cm);
     rowq(y0, k0, m0, c0);
-    for (int y = y0; y < y1; ++y) {
-      double kp, mp, cp;
-      rowq(y + 1, kp, mp, cp);
-      const double gxx = fma(4.0, k0, km + kp);
-      const double gyy = fma(2.0, m0, -(mm + mp));
-      const double gxy = cm - cp;
-      const long long a = x + (long long)m * y;
-      const double2* t2 = reinterpret_cast<const double2*>(t + 4 * a);
-      const double2* d2 = reinterpret_cast<const double2*>(dv + 4 * a);
-      const double2 ta = __ldg(t2), tb = __ldg(t2 + 1), da = __ldg(d2), db = __ldg(d2 + 1);
-      // components (k, p) = xx, xy, yx, yy
-      const double q0 = fma(-axx, gxx, ta.x), q1 = fma(-axy, gxy, ta.y);
-      const double q2 = fma(-axy, gxy, tb.x), q3 = fma(-axx, gyy, tb.y);
-      double2* o2 = reinterpret_cast<double2*>(q + 4 * a);
-      o2[0] = make_double2(q0, q1);
-      o2[1] = make_double2(q2, q3);
-      part[0] = fma(da.x, q0, part[0]);
-      part[0] = fma(da.y, q1, part[0]);
-      part[0] = fma(db.x, q2, part[0]);
-      part[0] = fma(db.y, q3, part[0]);
-      km = k0; mm = m0; cm = c0;
-      k0 = kp; m0 = mp; c0 = cp;
+    // kQU rows at a time: the row quantities of the next rows and the t, dv
+    // entries of the current ones are loaded together
+    for (int y = y0; y < y1; y += kQU) {
+      double kp[kQU], mp[kQU], cp[kQU];
+      double2 ta[kQU], tb[kQU], da[kQU], db[kQU];
+#pragma unroll
+      for (int u = 0; u < kQU; ++u) {
+        rowq(y + u + 1, kp[u], mp[u], cp[u]);
+        if (y + u < y1) {
+          const long long a = x + (long long)m * (y + u);
+          const double2* t2 = reinterpret_cast<const double2*>(t + 4 * a);
+          const double2* d2 = reinterpret_cast<const double2*>(dv + 4 * a);
+          ta[u] = __ldg(t2);
+          tb[u] = __ldg(t2 + 1);
+          da[u] = __ldg(d2);
+          db[u] = __ldg(d2 + 1);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kQU; ++u) {
+        if (y + u < y1) {
+          const double gxx = fma(4.0, k0, km + kp[u]);
+          const double gyy = fma(2.0, m0, -(mm + mp[u]));
+          const double gxy = cm - cp[u];
+          const long long a = x + (long long)m * (y + u);
+          // components (k, p) = xx, xy, yx, yy
+          const double q0 = fma(-axx, gxx, ta[u].x), q1 = fma(-axy, gxy, ta[u].y);
+          const double q2 = fma(-axy, gxy, tb[u].x), q3 = fma(-axx, gyy, tb[u].y);
+          double2* o2 = reinterpret_cast<double2*>(q + 4 * a);
+          o2[0] = make_double2(q0, q1);
+          o2[1] = make_double2(q2, q3);
+          part[0] = fma(da[u].x, q0, part[0]);
+          part[0] = fma(da[u].y, q1, part[0]);
+          part[0] = fma(db[u].x, q2, part[0]);
+          part[0] = fma(db[u].y, q3, part[0]);
+        }
+        km = k0; mm = m0; cm = c0;
+        k0 = kp[u]; m0 = mp[u]; c0 = cp[u];
+      }
     }
   }
   grid_reduce<1>(part, red);
