@@ -737,10 +737,13 @@ def batched_extra(args, opts, dcg, inputs, torch):
     return out
 
 
-def kernel_source_hash():
+def kernel_source_hash(files=None):
+    """Hash of the kernel sources (all of csrc/, or the named files): a DRAM
+    traffic figure in profiles/traffic.json counts only while the sources it
+    was captured on are unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_13429_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in sorted(files or os.listdir(csrc)):
         with open(os.path.join(csrc, fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -756,7 +759,7 @@ def roofline(dominant, dom, peaks, peak_src, fp64_peak):
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             tr = json.load(fh)
         ent = tr.get(dominant)
-        if ent and ent.get("source_hash") == kernel_source_hash():
+        if ent and ent.get("source_hash") == kernel_source_hash(ent.get("source_files")):
             traffic = ent["dram_bytes_per_launch"]
     except Exception:
         pass

@@ -722,6 +722,8 @@ __global__ void __launch_bounds__(256) k_ras_solve_tc(RasArgs ra, const float* _
       cur_cls = cls;
     }
     {
+      // thread keeps box b = tid % 128 (rows >= nb are zero) and walks the
+      // entries k = tid / 128, + 2, ...
       const int b = tid & 127;
       int node0 = 0;
       if (b < nb) node0 = __ldg(ra.origin + __ldg(ra.class_patches + first + b)).w;
@@ -976,9 +978,9 @@ __global__ void k_ras_update(const int* __restrict__ ysrc, const T* __restrict__
     }
     // multiplicities are products of 1s and 2s (a node lies in at most two
     // boxes per axis): the reciprocal is an exact power of two, picked
-    // without a division, so this equals z + s / mult
-    const T inv = mult == 1 ? (T)1 : mult == 2 ? (T)0.5 : mult == 4 ? (T)0.25 : (T)0.125;
-    z[a] += restricted ? s : s * inv;
+    // without a division, so s * inv = s / mult exactly and one FMA adds it
+    const T inv = (restricted || mult == 1) ? (T)1 : mult == 2 ? (T)0.5 : mult == 4 ? (T)0.25 : (T)0.125;
+    z[a] = fma(s, inv, z[a]);
   }
 }
 
