@@ -1151,9 +1151,14 @@ __device__ __forceinline__ void dst_stages(C2* buf, const C2* stw, int NP, int N
   }
 }
 
-// One pass: out = S in along one axis, line by line.
+// One pass: out = S in along one axis, line by line. Threads per CTA for
+// the long transforms (two lines per CTA, so the grid has only ncols / 2
+// CTAs): FP32 gains from one butterfly per thread and stage (512 threads at
+// 2(m+1) = 1024); FP64 is issue-bound and measured best at 256.
+template <typename T>
+constexpr int dst_threads() { return sizeof(T) == 4 ? 512 : 256; }
 template <typename T, bool AXIS0, int COLS>
-__global__ void __launch_bounds__(256) k_dst_pass(const T* __restrict__ in, T* __restrict__ out,
+__global__ void __launch_bounds__(dst_threads<T>()) k_dst_pass(const T* __restrict__ in, T* __restrict__ out,
                                                   const typename cplx<T>::type* __restrict__ tw, int m, int log2n2,
                                                   long long inner, long long ncols, T scale) {
   using C2 = typename cplx<T>::type;
@@ -1218,8 +1223,8 @@ void dst_pass(const T* in, T* out, const typename cplx<T>::type* tw, int m, int 
   if (log2n2 >= 9) {
     const unsigned grid = (unsigned)((ncols + 1) / 2);
     const size_t smem = dst_smem_bytes<T, 2>(log2n2);
-    if (inner == 1) k_dst_pass<T, true, 2><<<grid, 256, smem, s>>>(in, out, tw, m, log2n2, 1, ncols, scale);
-    else k_dst_pass<T, false, 2><<<grid, 256, smem, s>>>(in, out, tw, m, log2n2, inner, ncols, scale);
+    if (inner == 1) k_dst_pass<T, true, 2><<<grid, dst_threads<T>(), smem, s>>>(in, out, tw, m, log2n2, 1, ncols, scale);
+    else k_dst_pass<T, false, 2><<<grid, dst_threads<T>(), smem, s>>>(in, out, tw, m, log2n2, inner, ncols, scale);
   } else {
     const unsigned grid = (unsigned)((ncols + 7) / 8);
     const size_t smem = dst_smem_bytes<T, 8>(log2n2);
