@@ -681,7 +681,8 @@ __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, const T* 
 // gathered, rounded to BF16 and written in the same layout; one thread issues
 // npad/16 MMAs (M=128, N=npad, K=16) and commits them to an mbarrier; the
 // epilogue reads TMEM with tcgen05.ld (warp w: lanes 32(w%4).., half of the
-// columns) and stores results coalesced in the work item's layout [i][128].
+// columns) and stores results coalesced in the work item's entry-major
+// layout [i][nb] (a box-major layout, 32-byte runs per lane, measured slower).
 template <int D>
 __global__ void __launch_bounds__(256) k_ras_solve_tc(RasArgs ra, const float* __restrict__ rvec,
                                                        const __nv_bfloat16* __restrict__ invb, float* __restrict__ y) {

@@ -1,13 +1,14 @@
 // FP64 BSR SpMV for the pseudo-stress operator, with the deflation
 // embed/extract and the CG dot products fused into its prologue/epilogue.
 //
-// Mapping: a CTA owns 32 consecutive block rows; warp w computes scalar row
-// R(w) of each of them (lane = block row). Every warp therefore executes one
-// row pattern, so the structural zeros of the block (Section 3.1: the block is
-// (1/dt) mt D_d + kron(I_d, G), 10 of 16 entries in 2D, 33 of 81 in 3D) are
-// skipped without divergence. A lane reads the b contiguous doubles of its
-// block row chunk (one 32-byte sector in 2D) and the b doubles of x at the
-// column block.
+// Mapping in 2D (4 x 4 blocks): a CTA owns 32 consecutive block rows; warp w
+// computes scalar row R(w) of each of them (lane = block row). Every warp
+// therefore executes one row pattern, so the structural zeros of the block
+// (Section 3.1: the block is (1/dt) mt D_d + kron(I_d, G), 10 of 16 entries)
+// are skipped without divergence. A lane reads the 4 contiguous doubles of
+// its block row chunk (one 32-byte sector) and the 4 doubles of x at the
+// column block. 3D (9 x 9 blocks, 33 of 81 entries nonzero): k_spmv3 below,
+// one thread per structural nonzero.
 //
 // Variants (x operand / output):
 //   x            : y = A x
@@ -47,29 +48,6 @@ __device__ __forceinline__ double xval(const SpmvArgs& A, long long c, int col) 
   // XM_X_MINUS_VZ
   double v = __ldg(A.x + c * B + col);
   return diag ? __dsub_rn(v, __dmul_rn(A.isd, __ldg(A.zh + c))) : v;
-}
-
-// Sum over the block row of row R restricted to structural nonzeros.
-template <int D, int R, int XM>
-__device__ __forceinline__ double row_sum(const SpmvArgs& A, int j0, int j1) {
-  constexpr int B = D * D;
-  constexpr int k = R / D, i = R % D;
-  double acc = 0.0;
-  for (int j = j0; j < j1; ++j) {
-    const long long c = __ldg(A.col_idx + j);
-    const double* v = A.vals + (long long)j * (B * B) + R * B;
-    if (k == i) {
-#pragma unroll
-      for (int l = 0; l < D; ++l) acc = fma(__ldg(v + l * D + l), xval<D, XM>(A, c, l * D + l), acc);
-#pragma unroll
-      for (int q = 0; q < D; ++q)
-        if (q != k) acc = fma(__ldg(v + k * D + q), xval<D, XM>(A, c, k * D + q), acc);
-    } else {
-#pragma unroll
-      for (int q = 0; q < D; ++q) acc = fma(__ldg(v + k * D + q), xval<D, XM>(A, c, k * D + q), acc);
-    }
-  }
-  return acc;
 }
 
 // 2D: the 4 doubles of the row chunk and of the x block are 32-byte aligned
@@ -113,33 +91,14 @@ __device__ __forceinline__ double row_sum_2d(const SpmvArgs& A, int j0, int j1) 
 
 template <int D, int XM>
 __device__ __forceinline__ double row_dispatch(const SpmvArgs& A, int R, int j0, int j1) {
-  if constexpr (D == 2) {
-    switch (R) {
-      case 0: return row_sum_2d<0, XM>(A, j0, j1);
-      case 1: return row_sum_2d<1, XM>(A, j0, j1);
-      case 2: return row_sum_2d<2, XM>(A, j0, j1);
-      case 3: return row_sum_2d<3, XM>(A, j0, j1);
-      default: return 0.0;
-    }
-  }
+  static_assert(D == 2, "the 3D product is k_spmv3");
   switch (R) {
-    case 0: return row_sum<D, 0, XM>(A, j0, j1);
-    case 1: return row_sum<D, 1, XM>(A, j0, j1);
-    case 2: return row_sum<D, 2, XM>(A, j0, j1);
-    case 3: return row_sum<D, 3, XM>(A, j0, j1);
-    default: break;
+    case 0: return row_sum_2d<0, XM>(A, j0, j1);
+    case 1: return row_sum_2d<1, XM>(A, j0, j1);
+    case 2: return row_sum_2d<2, XM>(A, j0, j1);
+    case 3: return row_sum_2d<3, XM>(A, j0, j1);
+    default: return 0.0;
   }
-  if constexpr (D == 3) {
-    switch (R) {
-      case 4: return row_sum<D, 4, XM>(A, j0, j1);
-      case 5: return row_sum<D, 5, XM>(A, j0, j1);
-      case 6: return row_sum<D, 6, XM>(A, j0, j1);
-      case 7: return row_sum<D, 7, XM>(A, j0, j1);
-      case 8: return row_sum<D, 8, XM>(A, j0, j1);
-      default: break;
-    }
-  }
-  return 0.0;
 }
 
 template <int D, int XM, int OM, bool DOT>
