@@ -737,15 +737,26 @@ def batched_extra(args, opts, dcg, inputs, torch):
     return out
 
 
-def kernel_source_hash(files=None):
-    """Hash of the kernel sources (all of csrc/, or the named files): a DRAM
-    traffic figure in profiles/traffic.json counts only while the sources it
-    was captured on are unchanged."""
+def kernel_source_hash(files=None, functions=None):
+    """Hash of kernel sources: all of csrc/ (or the named files), or only the
+    text of the named device functions in them (from the line that declares
+    the function to its closing brace in column 0). A DRAM traffic figure in
+    profiles/traffic.json counts only while the code it was captured on is
+    unchanged."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_13429_gb300", "csrc")
     for fn in sorted(files or os.listdir(csrc)):
-        with open(os.path.join(csrc, fn), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, fn), "r", encoding="utf-8") as fh:
+            text = fh.read()
+        if not functions:
+            h.update(text.encode())
+            continue
+        for name in functions:
+            for mt in re.finditer(r"^(?:template <[^\n]*>\n)?(?:__global__|__device__)[^\n]*\b%s\(" % re.escape(name),
+                                  text, re.M):
+                end = text.find("\n}\n", mt.start())
+                h.update(text[mt.start():end + 3].encode())
     return h.hexdigest()[:16]
 
 
@@ -759,7 +770,7 @@ def roofline(dominant, dom, peaks, peak_src, fp64_peak):
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             tr = json.load(fh)
         ent = tr.get(dominant)
-        if ent and ent.get("source_hash") == kernel_source_hash(ent.get("source_files")):
+        if ent and ent.get("source_hash") == kernel_source_hash(ent.get("source_files"), ent.get("functions")):
             traffic = ent["dram_bytes_per_launch"]
     except Exception:
         pass
