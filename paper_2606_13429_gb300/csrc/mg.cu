@@ -1152,14 +1152,16 @@ __device__ __forceinline__ void dst_stages(C2* buf, const C2* stw, int NP, int N
   }
 }
 
-// One pass: out = S in along one axis, line by line. Threads per CTA for
-// the long transforms (two lines per CTA, so the grid has only ncols / 2
-// CTAs): FP32 gains from one butterfly per thread and stage (512 threads at
-// 2(m+1) = 1024); FP64 is issue-bound and measured best at 256.
+// Threads per CTA of the long-transform kernel (k_dst_half below: two lines
+// per CTA, so the grid has only ncols / 2 CTAs): FP32 gains from more warps
+// (512 threads), FP64 is issue-bound and measured best at 256.
 template <typename T>
 constexpr int dst_threads() { return sizeof(T) == 4 ? 512 : 256; }
+
+// One pass: out = S in along one axis, line by line (short transforms,
+// 2(m+1) <= 256, COLS lines per CTA).
 template <typename T, bool AXIS0, int COLS>
-__global__ void __launch_bounds__(dst_threads<T>()) k_dst_pass(const T* __restrict__ in, T* __restrict__ out,
+__global__ void __launch_bounds__(256) k_dst_pass(const T* __restrict__ in, T* __restrict__ out,
                                                   const typename cplx<T>::type* __restrict__ tw, int m, int log2n2,
                                                   long long inner, long long ncols, T scale) {
   using C2 = typename cplx<T>::type;
@@ -1216,16 +1218,121 @@ size_t dst_smem_bytes(int log2n2) {
   return sizeof(typename cplx<T>::type) * ((COLS / 2) * (N2 + (N2 >> 5)) + N2 / 2);
 }
 
-// one DST pass: 2 lines per CTA for long transforms (enough CTAs to fill the
-// GPU), 8 for short ones. The route takes 2(m+1) <= 2048.
+// Long sine transforms (N = m + 1 >= 256, lines a, b per CTA) through one
+// complex FFT of length N instead of 2N, about 40% fewer FP64 operations.
+// With x_0 = x_N = 0 and, for j = 1..N-1,
+//   y_j = sin(pi j / N) (x_j + x_{N-j}) + (x_j - x_{N-j}) / 2,   y_0 = 0,
+// the DFT Y_k = R_k + i I_k of y (k = 0..N/2-1) gives the sine sums
+//   X_{2k} = -I_k,   X_{2k+1} = X_{2k-1} + R_k,   X_1 = R_0 / 2
+// (the symmetric part of y carries the odd sums through sin(pi j/N) cos(2 pi j k/N)
+// = (sin(pi j (2k+1)/N) - sin(pi j (2k-1)/N)) / 2, the antisymmetric part the even
+// ones). Lines a and b form the real and imaginary parts of one complex
+// sequence, separated after the FFT through Z_k and conj(Z_{N-k}); the odd
+// outputs are prefix sums of R, formed by a Hillis-Steele scan in shared
+// memory (log2(N/2) steps; the rounding grows with the tree depth, as in the
+// FFT itself). Output scale sqrt(2/N) (the orthonormal S).
+template <typename T, bool AXIS0>
+__global__ void __launch_bounds__(dst_threads<T>()) k_dst_half(const T* __restrict__ in, T* __restrict__ out,
+                                                              const typename cplx<T>::type* __restrict__ tw, int m,
+                                                              int log2n2, long long inner, long long ncols, T scale) {
+  using C2 = typename cplx<T>::type;
+  extern __shared__ __align__(16) unsigned char dst_smem[];
+  const int log2n = log2n2 - 1, N = 1 << log2n, H = N >> 1, NP = N + (N >> 5);
+  C2* buf = reinterpret_cast<C2*>(dst_smem);  // [NP]: the length-N transform
+  C2* stw = buf + NP;                          // [N]: e^{-2 pi i j / (2N)}
+  T* scan = reinterpret_cast<T*>(stw + N);     // [2 buffers][2 lines][H]
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const long long la = 2LL * blockIdx.x, lb = la + 1;
+  const bool va = la < ncols, vb = lb < ncols;
+  auto gidx = [&](long long nb, int k) {
+    if (AXIS0) return nb * m + k;
+    const long long hi = nb / inner;
+    return hi * m * inner + (long long)k * inner + (nb - hi * inner);
+  };
+  auto xin = [&](bool v, long long nb, int j) {  // x_j, j = 1..N-1 (entry j - 1)
+    return v ? __ldg(in + gidx(nb, j - 1)) : (T)0;
+  };
+  for (int j = tid; j < N; j += bd) stw[j] = tw[j];
+  __syncthreads();
+  for (int j = tid; j < N; j += bd) {
+    C2 z{(T)0, (T)0};
+    if (j > 0) {
+      const T sj = -stw[j].y;  // sin(pi j / N)
+      const T a1 = xin(va, la, j), a2 = xin(va, la, N - j), b1 = xin(vb, lb, j), b2 = xin(vb, lb, N - j);
+      z.x = fma(sj, a1 + a2, (T)0.5 * (a1 - a2));
+      z.y = fma(sj, b1 + b2, (T)0.5 * (b1 - b2));
+    }
+    const int r = (int)(__brev((unsigned)j) >> (32 - log2n));
+    buf[dst_pad(r)] = z;
+  }
+  __syncthreads();
+  for (int st = 0; st < log2n; ++st) {
+    const int h = 1 << st;
+    for (int q = tid; q < H; q += bd) {
+      const int pos = q & (h - 1);
+      const int i0 = ((q >> st) << (st + 1)) + pos, i1 = i0 + h;
+      const C2 w = stw[pos << (log2n2 - 1 - st)];  // e^{-2 pi i pos / 2^(st+1)}
+      C2* e0 = buf + dst_pad(i0);
+      C2* e1 = buf + dst_pad(i1);
+      const C2 a = *e0, x = *e1;
+      const T tr = w.x * x.x - w.y * x.y, ti = w.x * x.y + w.y * x.x;
+      *e0 = C2{a.x + tr, a.y + ti};
+      *e1 = C2{a.x - tr, a.y - ti};
+    }
+    __syncthreads();
+  }
+  const T sc = (T)2 * scale;  // sqrt(2/N)
+  for (int k = tid; k < H; k += bd) {
+    const C2 zk = buf[dst_pad(k)], zn = buf[dst_pad((N - k) & (N - 1))];
+    const T ra = (T)0.5 * (zk.x + zn.x), ia = (T)0.5 * (zk.y - zn.y);
+    const T rb = (T)0.5 * (zk.y + zn.y), ib = (T)0.5 * (zn.x - zk.x);
+    if (k > 0) {
+      if (va) out[gidx(la, 2 * k - 1)] = -ia * sc;
+      if (vb) out[gidx(lb, 2 * k - 1)] = -ib * sc;
+    }
+    scan[k] = k == 0 ? (T)0.5 * ra : ra;
+    scan[H + k] = k == 0 ? (T)0.5 * rb : rb;
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int off = 1; off < H; off <<= 1) {
+    const T* src = scan + cur * 2 * H;
+    T* dst = scan + (cur ^ 1) * 2 * H;
+    for (int t = tid; t < 2 * H; t += bd) {
+      const int k = t & (H - 1);
+      dst[t] = k >= off ? src[t] + src[t - off] : src[t];
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  const T* fin = scan + cur * 2 * H;
+  for (int t = tid; t < 2 * H; t += bd) {
+    const int k = t & (H - 1);
+    if (t < H) {
+      if (va) out[gidx(la, 2 * k)] = fin[t] * sc;
+    } else if (vb) {
+      out[gidx(lb, 2 * k)] = fin[t] * sc;
+    }
+  }
+}
+
+template <typename T>
+size_t dst_half_smem_bytes(int log2n2) {
+  const size_t N = (size_t)1 << (log2n2 - 1);
+  return sizeof(typename cplx<T>::type) * ((N + (N >> 5)) + N) + sizeof(T) * 2 * N;
+}
+
+// one DST pass: long transforms (m + 1 >= 256) by the half-length FFT, two
+// lines per CTA (enough CTAs to fill the GPU); short ones by the length-2N
+// FFT, 8 lines per CTA. The route takes 2(m+1) <= 2048.
 template <typename T>
 void dst_pass(const T* in, T* out, const typename cplx<T>::type* tw, int m, int log2n2, long long inner,
               long long ncols, T scale, cudaStream_t s) {
   if (log2n2 >= 9) {
     const unsigned grid = (unsigned)((ncols + 1) / 2);
-    const size_t smem = dst_smem_bytes<T, 2>(log2n2);
-    if (inner == 1) k_dst_pass<T, true, 2><<<grid, dst_threads<T>(), smem, s>>>(in, out, tw, m, log2n2, 1, ncols, scale);
-    else k_dst_pass<T, false, 2><<<grid, dst_threads<T>(), smem, s>>>(in, out, tw, m, log2n2, inner, ncols, scale);
+    const size_t smem = dst_half_smem_bytes<T>(log2n2);
+    if (inner == 1) k_dst_half<T, true><<<grid, dst_threads<T>(), smem, s>>>(in, out, tw, m, log2n2, 1, ncols, scale);
+    else k_dst_half<T, false><<<grid, dst_threads<T>(), smem, s>>>(in, out, tw, m, log2n2, inner, ncols, scale);
   } else {
     const unsigned grid = (unsigned)((ncols + 7) / 8);
     const size_t smem = dst_smem_bytes<T, 8>(log2n2);
@@ -1238,10 +1345,10 @@ void dst_pass(const T* in, T* out, const typename cplx<T>::type* tw, int m, int 
 // transform the route takes (2(m+1) = 2048)
 template <typename T>
 int set_dst_smem() {
-  const int big = (int)dst_smem_bytes<T, 2>(11), small = (int)dst_smem_bytes<T, 8>(8);
+  const int big = (int)dst_half_smem_bytes<T>(11), small = (int)dst_smem_bytes<T, 8>(8);
   const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, true, 2>, attr, big));
-  DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, false, 2>, attr, big));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_half<T, true>, attr, big));
+  DCG_CUDA(cudaFuncSetAttribute(k_dst_half<T, false>, attr, big));
   DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, true, 8>, attr, small));
   DCG_CUDA(cudaFuncSetAttribute(k_dst_pass<T, false, 8>, attr, small));
   return DCG_OK;
