@@ -52,3 +52,28 @@ def test_single_rank_job_time():
     import bench
     elapsed, value = bench.job_time(120.0, 4, 1, torch, device="cpu")
     assert elapsed == 120.0 and value == pytest.approx(0.03)
+
+
+def test_traffic_records_name_existing_kernels():
+    """Every DRAM-traffic record names source files and device functions that
+    exist (each function found once), so its source hash can be checked; a
+    record whose kernel changed is ignored by the bench (hash mismatch), not
+    misattributed."""
+    import json
+    import os
+    import re
+    import bench
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with open(os.path.join(root, "profiles", "traffic.json")) as fh:
+        records = json.load(fh)
+    csrc = os.path.join(root, "paper_2606_13429_gb300", "csrc")
+    for cls, ent in records.items():
+        assert ent["dram_bytes_per_launch"] > 0, cls
+        for fn in ent.get("source_files", []):
+            text = open(os.path.join(csrc, fn), encoding="utf-8").read()
+            for name in ent.get("functions", []):
+                found = re.findall(r"^(?:template <[^\n]*>\n)?(?:__global__|__device__)[^\n]*\b%s\(" % re.escape(name),
+                                   text, re.M)
+                assert len(found) == 1, (cls, name, len(found))
+        h = bench.kernel_source_hash(ent.get("source_files"), ent.get("functions"))
+        assert isinstance(h, str) and len(h) == 16
