@@ -705,8 +705,9 @@ __global__ void __launch_bounds__(kRasThreads) k_ras_solve(RasArgs ra, const T* 
   }
 }
 
-// (1') Tensor-core variant (tcgen05, kind::f16): per work item of up to 128
-// boxes, D[128 boxes x npad] = G^T[128 x npad] * inv^T with BF16 operands and
+// (1') Tensor-core variant (tcgen05, kind::f16): per work item of kTcBatch
+// boxes (rows up to 128 of the M = 128 MMA, the rest zero),
+// D[128 x npad] = G^T[128 x npad] * inv^T with BF16 operands and
 // FP32 accumulation in TMEM (the inverse is symmetric, so inv^T = inv). The
 // class inverse is stored at setup in the canonical K-major BF16 layout and
 // brought into shared memory with one bulk copy; the residual tile is
